@@ -1,0 +1,190 @@
+/*
+ * pairf12.h -- C ABI of the GB300 (sm_103a) pair-F12 library (libpairf12.so).
+ *
+ * What it computes (Kumar, Neese, Valeev, arXiv 2008.03237): for every F12
+ * pair P = (i, j), i <= j, of localised occupied orbitals, the amplitude term
+ * of the pair-specific F12 correction in the spin-independent PNO basis.
+ *
+ *   1. local DF with the pair's auxiliary metric (Sec. "F12 integral
+ *      transformations": integrals of i and j are sieved onto the pair domain
+ *      and recombined through local density fitting):
+ *         J_g = L L^T (FP64 Cholesky),  C_x = A^g_x J_g^{-1},  x in {i, j}
+ *   2. robust (Dunlap) fit of the F12 pair integral (Eq. V with the F12 kernel
+ *      fitted from the Coulomb-metric coefficients):
+ *         K = A^f_i C_j^T + C_i A^f_j^T - C_i J_f C_j^T       (p x p)
+ *   3. PNO transform (Sec. "Pair-natural orbitals", "SOMO handling"):
+ *         V = Q^T K Q                                          (k x k)
+ *   4. amplitude contraction (term 1/2 V^{ij}_{ab} t^{ab}_{ij} of Eq. Vtilde):
+ *         d = sum V_ab T_ab,  x = sum V_ab T_ba
+ *   5. spin cases (Eqs. F12energy_sf*, ROHF rules after them):
+ *         e_ab = n_ab (3d + x)/8, e_aa = n_aa (d - x)/4, e_bb = n_bb (d - x)/4
+ *      with (n_ab, n_aa, n_bb) = DOMO-DOMO (2,1,1), (1,0,0) if i == j;
+ *      SOMO-DOMO (1,1,0); SOMO-SOMO (0,1,0), (0,0,0) if i == j.
+ *   6. E = sum of all pair energies, FP64, fixed order (deterministic).
+ *
+ * The device pipeline evaluates steps 1-3 in the exactly equivalent order
+ * At = Q^T A (k x m), Ct = At^g J_g^{-1}, V = At^f_i Ct_j^T + Ct_i At^f_j^T -
+ * (Ct_i J_f) Ct_j^T, so the FP64 solves run on k right-hand sides, not p.
+ * The Cholesky factorisation, both triangular solves and all energy sums are
+ * always FP64.  The projections and the J_f / V products follow `precision`.
+ *
+ * Conventions for every entry point
+ *   - Return 0 on success or a negative PF12_ERR_* code; pf12_last_error()
+ *     gives a message.  No call aborts the process.
+ *   - Tensor arguments are caller-owned device buffers (float64, row-major)
+ *     unless marked "host".  The library never frees them; they must stay
+ *     valid until the next pf12_upload_pairs or pf12_destroy.
+ *   - The library owns its workspace, pair metadata and CUDA graph.
+ *   - Calls are ordered on the context's stream; only the calls that return
+ *     host values (pf12_energy's E_host, pf12_pair_status, pf12_stats)
+ *     synchronise that stream.
+ */
+#ifndef PAIRF12_H
+#define PAIRF12_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PF12_OK 0
+#define PF12_ERR_INVALID_ARG (-1) /* bad size, index, offset, null pointer, call order */
+#define PF12_ERR_NOT_SPD (-2)     /* a pair's J_g has a pivot <= 0 (see pf12_pair_status) */
+#define PF12_ERR_OOM (-3)         /* workspace allocation failed or exceeds workspace_bytes */
+#define PF12_ERR_CUDA (-4)        /* a CUDA runtime call failed */
+#define PF12_ERR_TIMEOUT (-5)     /* a bounded device wait ran out */
+#define PF12_ERR_NONFINITE (-6)   /* a pair energy is NaN or Inf */
+#define PF12_ERR_UNSUPPORTED (-7) /* option not built into this library */
+
+/* per-pair status codes written by the device (pf12_pair_status) */
+#define PF12_PAIR_OK 0
+#define PF12_PAIR_NOT_SPD 1      /* Cholesky pivot <= 0 or not finite */
+#define PF12_PAIR_NONFINITE 2    /* V or the pair energy is not finite */
+
+/* Arithmetic of the projections (Q^T A) and of the J_f / V products.
+ * FP64 Cholesky, solves and energy sums in every mode. */
+typedef enum {
+  PF12_FP64 = 0,       /* everything FP64 (plain mode) */
+  PF12_MIXED_FP32 = 2  /* FP32 products, FP32 partial sums over 32-wide K chunks
+                          promoted to FP64 accumulators */
+} pf12_precision;
+
+typedef struct pf12_ctx pf12_ctx; /* opaque, library-owned */
+
+typedef struct {
+  int precision;           /* pf12_precision */
+  void* cuda_stream;       /* cudaStream_t all work is ordered on; NULL = legacy stream */
+  size_t workspace_bytes;  /* cap on library-owned device workspace; 0 = no cap */
+  int deterministic;       /* reserved: energy sums are always fixed-order */
+  const char* tuner_cache; /* path of the autotuner's cache file, or NULL (no cache) */
+} pf12_opts;
+
+/* Packed ("plain mode") per-pair tensors.  Pair P's blocks start at element
+ * offset off_xx[P] of the matching buffer:
+ *   Ag_i, Ag_j, Af_i, Af_j : p x m   at off_pm[P]  (DF factors of orbital i / j,
+ *                                                   Coulomb g and F12 f kernels)
+ *   Jg, Jf                 : m x m   at off_mm[P]  (SPD auxiliary metrics)
+ *   Q                      : p x k   at off_pk[P]  (PAO -> PNO coefficients)
+ *   T                      : k x k   at off_kk[P]  (PNO amplitudes t^{ab}_{ij})
+ * Offsets are host arrays, element (not byte) offsets, multiples of 2 (16-byte
+ * aligned), and each block must lie inside its buffer (len_xx elements).
+ * Device pointers must be 16-byte aligned. */
+typedef struct {
+  const double* Ag_i;
+  const double* Ag_j;
+  const double* Af_i;
+  const double* Af_j;
+  const double* Jg;
+  const double* Jf;
+  const double* Q;
+  const double* T;
+  const int64_t* off_pm; /* host */
+  const int64_t* off_mm; /* host */
+  const int64_t* off_pk; /* host */
+  const int64_t* off_kk; /* host */
+  int64_t len_pm, len_mm, len_pk, len_kk;
+} pf12_tensors;
+
+typedef struct {
+  double ms_fit;         /* device time of the last pf12_fit (CUDA events) */
+  double ms_energy;      /* device time of the last pf12_energy reduction */
+  double ms_backward;    /* device time of the last pf12_backward */
+  double flops_fp64;     /* algorithmic FP64 flops of one forward pass: sum m^3/3 + 4 k m^2
+                            (+ the mixable flops in PF12_FP64 mode) */
+  double flops_mixed;    /* algorithmic flops of the mixable part: 8pkm + 2km^2 + 4k^2m */
+  double bytes_in;       /* algorithmic input bytes of one forward pass */
+  int64_t n_pairs;
+  int32_t n_ctas;        /* persistent CTAs of the fused pair kernel */
+  int32_t launches_fit;  /* kernels launched by one pf12_fit */
+  int32_t tile_config;   /* autotuner choice (index) */
+  int32_t graph_used;    /* 1 when pf12_fit replays a captured CUDA graph */
+} pf12_stats_t;
+
+/* Create a context.  opts may be NULL (FP64, legacy stream, no cap). */
+int pf12_create(pf12_ctx** ctx, const pf12_opts* opts);
+
+/* Re-target the stream for subsequent calls (e.g. torch's current stream). */
+int pf12_set_stream(pf12_ctx* ctx, void* cuda_stream);
+
+/* Register the pair list and the packed tensors (Sec. "Pair-screenings": the
+ * F12 pair list; Sec. "F12 integral transformations": the pair domains).
+ *   n_orb, orb_kind (host, n_orb): 0 = DOMO, 1 = SOMO
+ *   pi, pj (host, n_pairs): orbital indices, 0 <= pi <= pj < n_orb
+ *   n_pao, n_pno, n_aux (host, n_pairs): p >= 1, 1 <= k <= p, m >= 1,
+ *     m <= 4096, k <= 256
+ *   t: packed tensors (see pf12_tensors)
+ * Copies metadata to the device, orders pairs by cost for the persistent
+ * kernel and sizes the workspace.  Invalidates any captured graph. */
+int pf12_upload_pairs(pf12_ctx* ctx, int32_t n_orb, const int8_t* orb_kind, int64_t n_pairs,
+                      const int32_t* pi, const int32_t* pj, const int32_t* n_pao,
+                      const int32_t* n_pno, const int32_t* n_aux, const pf12_tensors* t);
+
+/* Steps 1-4 for every pair in one persistent fused launch (replayed from a
+ * captured CUDA graph after the first call): projections, FP64 Cholesky of
+ * J_g, FP64 solves, robust fit to V (kept in the context), and the pair
+ * contractions d, x.  A pair whose J_g is not SPD gets status NOT_SPD and NaN
+ * energies; the call itself still returns 0 (query pf12_pair_status). */
+int pf12_fit(pf12_ctx* ctx);
+
+/* Copy V^{ij} of every pair (k x k, row-major) into V_dev at the pair's off_kk
+ * offset (same layout as T).  Requires a previous pf12_fit. */
+int pf12_build_v(pf12_ctx* ctx, double* V_dev);
+
+/* Step 5-6: spin-case pair energies and the total.
+ *   e_pair_dev (device, n_pairs x 3, may be NULL): (e_ab, e_aa, e_bb) per pair
+ *   E_host (host, may be NULL): the FP64 total, summed in a fixed order
+ * Returns PF12_ERR_NOT_SPD / PF12_ERR_NONFINITE when any pair failed (E_host
+ * is then NaN).  Requires a previous pf12_fit. */
+int pf12_energy(pf12_ctx* ctx, double* e_pair_dev, double* E_host);
+
+/* Adjoint of dE * E with respect to the DF factors, PNO coefficients and
+ * amplitudes (J_g, J_f are constants).  Recomputes the forward intermediates
+ * pair by pair instead of storing them.  Outputs use the input layouts
+ * (off_pm / off_pk / off_kk) and are overwritten (not accumulated); any output
+ * pointer may be NULL to skip it.  Formulas, with alpha, beta the weights of
+ * E_P = alpha d + beta x:
+ *   G_V = alpha T + beta T^T,   dT = alpha V + beta V^T
+ *   dAf_i = Q G_V Ct_j,  dAf_j = Q G_V^T Ct_i
+ *   dAg_i = Q G_V Z_j^T, dAg_j = Q G_V^T Z_i^T, Z_x^T = (At^f_x - Ct_x J_f) J_g^{-1}
+ *   dQ = (Af_i Ct_j^T + Ag_i Z_j) G_V^T + (Af_j Ct_i^T + Ag_j Z_i) G_V */
+int pf12_backward(pf12_ctx* ctx, double dE, double* dAg_i, double* dAg_j, double* dAf_i,
+                  double* dAf_j, double* dQ, double* dT);
+
+/* Per-pair status (host, n_pairs) of the last pf12_fit / pf12_backward. */
+int pf12_pair_status(pf12_ctx* ctx, int32_t* status_host);
+
+/* Timers, flop and byte counts of the last calls. */
+int pf12_stats(pf12_ctx* ctx, pf12_stats_t* out);
+
+/* Message of the last error on this context (never NULL). */
+const char* pf12_last_error(const pf12_ctx* ctx);
+
+/* Release the context's workspace, graph and metadata. */
+void pf12_destroy(pf12_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAIRF12_H */

@@ -1,0 +1,196 @@
+"""GB300-native pair-F12 energy path (arXiv 2008.03237) -- Python binding.
+
+Every step of the path runs in libpairf12.so (hand-written sm_103a kernels);
+this module only marshals arguments through the C ABI of include/pairf12.h and
+wraps the energy in a torch.autograd.Function whose backward calls the
+library's adjoint kernel.  PyTorch supplies device memory and streams.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+__all__ = ["PairF12", "PairF12Energy", "pair_f12_energy", "Pf12Error", "lib"]
+
+
+class Pf12Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pf12 error {code} ({_lib.ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+def lib():
+    return _lib.load()
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _i64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+
+
+def _ptr(arr, ctype):
+    return arr.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _dev(t, name):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+TENSOR_NAMES = ("Agi", "Agj", "Afi", "Afj", "Jg", "Jf", "Q", "T")
+_C_NAMES = ("Ag_i", "Ag_j", "Af_i", "Af_j", "Jg", "Jf", "Q", "T")
+
+
+class PairF12:
+    """One library context: a pair list, its packed device tensors and workspace.
+
+    precision: "fp64" (plain mode) or "mixed_fp32".  FP64 Cholesky, solves and
+    energy sums in both."""
+
+    def __init__(self, precision="fp64", workspace_bytes=0, stream=None):
+        self._L = lib()
+        opts = _lib.Opts(_lib.PRECISION[precision], None, int(workspace_bytes), 1, None)
+        h = ctypes.c_void_p()
+        self._check(self._L.pf12_create(ctypes.byref(h), ctypes.byref(opts)), None)
+        self._h = h
+        self.precision = precision
+        self._keep = None
+        self.n_pairs = 0
+
+    # -------------------------------------------------------------- plumbing
+    def _check(self, code, h=0):
+        if code != _lib.PF12_OK:
+            hh = self._h if h == 0 else h
+            msg = self._L.pf12_last_error(hh).decode() if hh else "pf12_create failed"
+            raise Pf12Error(code, msg)
+
+    def _stream(self):
+        s = torch.cuda.current_stream().cuda_stream
+        self._check(self._L.pf12_set_stream(self._h, ctypes.c_void_p(s)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.pf12_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- C ABI calls
+    def upload_pairs(self, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, tensors, offsets):
+        """tensors: dict of packed float64 CUDA tensors (TENSOR_NAMES);
+        offsets: dict with off_pm/off_mm/off_pk/off_kk (int64 arrays)."""
+        self._stream()
+        kind = np.ascontiguousarray(np.asarray(orb_kind, dtype=np.int8))
+        meta = [_i32(pi), _i32(pj), _i32(n_pao), _i32(n_pno), _i32(n_aux)]
+        offs = {n: _i64(offsets[n]) for n in ("off_pm", "off_mm", "off_pk", "off_kk")}
+        tt = _lib.Tensors()
+        for py, c in zip(TENSOR_NAMES, _C_NAMES):
+            setattr(tt, c, _dev(tensors[py], py))
+        for n in offs:
+            setattr(tt, n, _ptr(offs[n], ctypes.c_int64))
+        tt.len_pm = tensors["Agi"].numel()
+        tt.len_mm = tensors["Jg"].numel()
+        tt.len_pk = tensors["Q"].numel()
+        tt.len_kk = tensors["T"].numel()
+        n = len(meta[0])
+        self._check(self._L.pf12_upload_pairs(
+            self._h, int(n_orb), _ptr(kind, ctypes.c_int8), n,
+            *[_ptr(a, ctypes.c_int32) for a in meta], ctypes.byref(tt)))
+        self._keep = (tensors, offs, meta, kind)
+        self.n_pairs = n
+        self.len_kk = tt.len_kk
+
+    def fit(self):
+        self._stream()
+        self._check(self._L.pf12_fit(self._h))
+
+    def build_v(self, V=None):
+        self._stream()
+        if V is None:
+            V = torch.zeros(self.len_kk, dtype=torch.float64, device="cuda")
+        self._check(self._L.pf12_build_v(self._h, _dev(V, "V")))
+        return V
+
+    def energy(self, e_pair=None, want_host=True, check=True):
+        """Returns (E, e_pair): E a Python float (FP64, fixed-order total)."""
+        self._stream()
+        if e_pair is None:
+            e_pair = torch.empty((self.n_pairs, 3), dtype=torch.float64, device="cuda")
+        E = ctypes.c_double(float("nan"))
+        code = self._L.pf12_energy(self._h, _dev(e_pair, "e_pair"),
+                                   ctypes.byref(E) if want_host else None)
+        if check:
+            self._check(code)
+        return E.value, e_pair
+
+    def backward(self, dE=1.0, grads=None):
+        """Writes dE * dE_F12/d{Agi,Agj,Afi,Afj,Q,T} into grads (dict of packed
+        float64 CUDA tensors shaped like the inputs; missing keys are skipped)."""
+        self._stream()
+        g = grads or {}
+        args = [_dev(g.get(n), n) for n in ("Agi", "Agj", "Afi", "Afj", "Q", "T")]
+        self._check(self._L.pf12_backward(self._h, float(dE), *args))
+        return g
+
+    def pair_status(self):
+        st = np.zeros(max(self.n_pairs, 1), dtype=np.int32)
+        self._check(self._L.pf12_pair_status(self._h, _ptr(st, ctypes.c_int32)))
+        return st[:self.n_pairs]
+
+    def stats(self):
+        s = _lib.Stats()
+        self._check(self._L.pf12_stats(self._h, ctypes.byref(s)))
+        return {n: getattr(s, n) for n, _ in _lib.Stats._fields_}
+
+
+class PairF12Energy(torch.autograd.Function):
+    """E_F12 (sum of all pair energies) as a differentiable function of the DF
+    factors, PNO coefficients and amplitudes; J_g and J_f are constants.
+
+    forward(ctx, Agi, Agj, Afi, Afj, Jg, Jf, Q, T, meta) with meta a dict of
+    n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, off_pm, off_mm, off_pk,
+    off_kk and optionally precision.  backward recomputes V per pair in the
+    library's adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, Agi, Agj, Afi, Afj, Jg, Jf, Q, T, meta):
+        eng = PairF12(meta.get("precision", "fp64"))
+        tensors = dict(zip(TENSOR_NAMES, (Agi, Agj, Afi, Afj, Jg, Jf, Q, T)))
+        eng.upload_pairs(meta["n_orb"], meta["orb_kind"], meta["pi"], meta["pj"], meta["n_pao"],
+                         meta["n_pno"], meta["n_aux"], tensors, meta)
+        eng.fit()
+        E, _ = eng.energy()
+        ctx.eng = eng
+        ctx.shapes = [t.shape for t in (Agi, Agj, Afi, Afj, Q, T)]
+        return torch.tensor(E, dtype=torch.float64, device=Agi.device)
+
+    @staticmethod
+    def backward(ctx, gE):
+        eng = ctx.eng
+        need = ctx.needs_input_grad
+        names = ("Agi", "Agj", "Afi", "Afj", "Q", "T")
+        idx = (0, 1, 2, 3, 6, 7)
+        grads = {}
+        for n, i, shp in zip(names, idx, ctx.shapes):
+            if need[i]:
+                grads[n] = torch.zeros(shp, dtype=torch.float64, device=gE.device)
+        eng.backward(float(gE), grads)
+        out = [grads.get(n) for n in names]
+        eng.close()
+        return out[0], out[1], out[2], out[3], None, None, out[4], out[5], None
+
+
+def pair_f12_energy(Agi, Agj, Afi, Afj, Jg, Jf, Q, T, meta):
+    return PairF12Energy.apply(Agi, Agj, Afi, Afj, Jg, Jf, Q, T, meta)

@@ -1,0 +1,435 @@
+// Host side of the C ABI declared in include/pairf12.h: argument checks, pair
+// metadata and cost-sorted work queue, workspace sizing, CUDA-graph capture of
+// the fused forward launch, deterministic energy total, timers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/pairf12.h"
+#include "pf12_internal.h"
+
+using pf12::PairDesc;
+
+struct pf12_ctx {
+  int precision = PF12_FP64;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  size_t ws_cap = 0;
+  std::string err = "no error";
+  int n_sm = 0;
+
+  // pair metadata
+  int64_t n_pairs = 0;
+  bool uploaded = false, fitted = false;
+  pf12_tensors t{};
+  std::vector<int64_t> off_kk;
+  std::vector<int32_t> pk;  // n_pno per pair (caller order)
+  PairDesc* d_desc = nullptr;
+  double* d_V = nullptr;        // len_kk
+  double* d_epair = nullptr;    // 3 n
+  double* d_dx = nullptr;       // 2 n
+  int32_t* d_status = nullptr;  // n
+  double* d_out3 = nullptr;     // energy total
+  int32_t* d_counter = nullptr;
+  double* d_work = nullptr;
+  size_t work_bytes = 0;
+  int64_t ws_stride = 0, ws_stride_bwd = 0;
+  int n_ctas = 0, n_ctas_bwd = 0;
+  int64_t max_fwd_ws = 0, max_bwd_ws = 0;
+
+  // graph of the forward launch
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+
+  // timers
+  cudaEvent_t ev[6] = {};
+  bool t_fit = false, t_energy = false, t_bwd = false;
+  double flops64 = 0, flops_mix = 0, bytes_in = 0;
+};
+
+namespace {
+
+int fail(pf12_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(pf12_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, PF12_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PF12_CUDA(ctx, call)                               \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+void free_pairs(pf12_ctx* c) {
+  cudaFree(c->d_desc);
+  cudaFree(c->d_V);
+  cudaFree(c->d_epair);
+  cudaFree(c->d_dx);
+  cudaFree(c->d_status);
+  cudaFree(c->d_out3);
+  cudaFree(c->d_counter);
+  cudaFree(c->d_work);
+  c->d_desc = nullptr;
+  c->d_V = c->d_epair = c->d_dx = c->d_out3 = c->d_work = nullptr;
+  c->d_status = c->d_counter = nullptr;
+  c->work_bytes = 0;
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+  c->uploaded = c->fitted = false;
+  c->n_pairs = 0;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+pf12::FwdParams fwd_params(pf12_ctx* c) {
+  pf12::FwdParams f{};
+  f.Agi = c->t.Ag_i;
+  f.Agj = c->t.Ag_j;
+  f.Afi = c->t.Af_i;
+  f.Afj = c->t.Af_j;
+  f.Jg = c->t.Jg;
+  f.Jf = c->t.Jf;
+  f.Q = c->t.Q;
+  f.T = c->t.T;
+  f.desc = c->d_desc;
+  f.n_pairs = c->n_pairs;
+  f.V = c->d_V;
+  f.e_pair = c->d_epair;
+  f.dx = c->d_dx;
+  f.status = c->d_status;
+  f.work = c->d_work;
+  f.ws_stride = c->ws_stride;
+  f.counter = c->d_counter;
+  return f;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pf12_create(pf12_ctx** out, const pf12_opts* o) {
+  if (!out) return PF12_ERR_INVALID_ARG;
+  *out = nullptr;
+  pf12_ctx* c = new pf12_ctx();
+  if (o) {
+    if (o->precision != PF12_FP64 && o->precision != PF12_MIXED_FP32) {
+      delete c;
+      return PF12_ERR_UNSUPPORTED;
+    }
+    c->precision = o->precision;
+    c->stream = static_cast<cudaStream_t>(o->cuda_stream);
+    c->ws_cap = o->workspace_bytes;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
+  if (e != cudaSuccess) {
+    delete c;
+    return PF12_ERR_CUDA;
+  }
+  *out = c;
+  return PF12_OK;
+}
+
+int pf12_set_stream(pf12_ctx* c, void* s) {
+  if (!c) return PF12_ERR_INVALID_ARG;
+  c->stream = static_cast<cudaStream_t>(s);
+  return PF12_OK;
+}
+
+int pf12_upload_pairs(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_pairs,
+                      const int32_t* pi, const int32_t* pj, const int32_t* n_pao,
+                      const int32_t* n_pno, const int32_t* n_aux, const pf12_tensors* t) {
+  if (!c) return PF12_ERR_INVALID_ARG;
+  free_pairs(c);
+  if (n_pairs < 0 || n_orb < 0) return fail(c, PF12_ERR_INVALID_ARG, "negative count");
+  if (n_pairs > 0 && (!kind || !pi || !pj || !n_pao || !n_pno || !n_aux || !t))
+    return fail(c, PF12_ERR_INVALID_ARG, "null metadata pointer");
+  if (n_pairs > 0) {
+    const double* ptrs[8] = {t->Ag_i, t->Ag_j, t->Af_i, t->Af_j, t->Jg, t->Jf, t->Q, t->T};
+    for (const double* p : ptrs)
+      if (!p || !aligned16(p)) return fail(c, PF12_ERR_INVALID_ARG, "tensor pointer null or not 16-byte aligned");
+    if (!t->off_pm || !t->off_mm || !t->off_pk || !t->off_kk)
+      return fail(c, PF12_ERR_INVALID_ARG, "null offset array");
+  }
+  for (int32_t o = 0; o < n_orb; ++o)
+    if (kind[o] != 0 && kind[o] != 1) return fail(c, PF12_ERR_INVALID_ARG, "orb_kind must be 0 or 1");
+
+  std::vector<PairDesc> desc(n_pairs);
+  std::vector<double> cost(n_pairs);
+  double f64 = 0, fmix = 0, bytes = 0;
+  int64_t max_fwd = 0, max_bwd = 0;
+  c->off_kk.assign(n_pairs, 0);
+  c->pk.assign(n_pairs, 0);
+  for (int64_t P = 0; P < n_pairs; ++P) {
+    const int32_t i = pi[P], j = pj[P], p = n_pao[P], k = n_pno[P], m = n_aux[P];
+    char buf[160];
+    if (i < 0 || j < 0 || i >= n_orb || j >= n_orb || i > j) {
+      snprintf(buf, sizeof buf, "pair %lld: need 0 <= i <= j < n_orb", (long long)P);
+      return fail(c, PF12_ERR_INVALID_ARG, buf);
+    }
+    if (p < 1 || k < 1 || m < 1 || k > p || m > pf12::kMaxAux || k > pf12::kMaxPno) {
+      snprintf(buf, sizeof buf, "pair %lld: sizes p=%d k=%d m=%d out of range", (long long)P, p, k, m);
+      return fail(c, PF12_ERR_INVALID_ARG, buf);
+    }
+    const int64_t offs[4] = {t->off_pm[P], t->off_mm[P], t->off_pk[P], t->off_kk[P]};
+    const int64_t sizes[4] = {(int64_t)p * m, (int64_t)m * m, (int64_t)p * k, (int64_t)k * k};
+    const int64_t lens[4] = {t->len_pm, t->len_mm, t->len_pk, t->len_kk};
+    for (int q = 0; q < 4; ++q)
+      if (offs[q] < 0 || (offs[q] & 1) || offs[q] + sizes[q] > lens[q]) {
+        snprintf(buf, sizeof buf, "pair %lld: offset %d misaligned or block outside its buffer", (long long)P, q);
+        return fail(c, PF12_ERR_INVALID_ARG, buf);
+      }
+    PairDesc& d = desc[P];
+    d.off_pm = offs[0];
+    d.off_mm = offs[1];
+    d.off_pk = offs[2];
+    d.off_kk = offs[3];
+    d.p = p;
+    d.k = k;
+    d.m = m;
+    d.pair = (int32_t)P;
+    const int ki = kind[i], kj = kind[j];
+    const int ai = 1, bi = ki == 0, aj = 1, bj = kj == 0;
+    if (i == j) {
+      d.n_ab = (int8_t)(ai * bi);
+      d.n_aa = d.n_bb = 0;
+    } else {
+      d.n_ab = (int8_t)(ai * bj + aj * bi);
+      d.n_aa = (int8_t)(ai * aj);
+      d.n_bb = (int8_t)(bi * bj);
+    }
+    d.w_alpha = 3.0f * d.n_ab / 8.0f + (d.n_aa + d.n_bb) / 4.0f;
+    d.w_beta = d.n_ab / 8.0f - (d.n_aa + d.n_bb) / 4.0f;
+    d.pad = 0;
+    const double dm = m, dk = k, dp = p;
+    const double c64 = dm * dm * dm / 3.0 + 4.0 * dk * dm * dm;
+    const double cmix = 8.0 * dp * dk * dm + 2.0 * dk * dm * dm + 4.0 * dk * dk * dm;
+    cost[P] = c64 + cmix / 8.0;
+    f64 += c64;
+    fmix += cmix;
+    bytes += 8.0 * (4.0 * dp * dm + 2.0 * dm * dm + dp * dk + dk * dk);
+    max_fwd = std::max(max_fwd, pf12::fwd_ws(p, k, m));
+    max_bwd = std::max(max_bwd, pf12::bwd_ws(p, k, m));
+    c->off_kk[P] = offs[3];
+    c->pk[P] = k;
+  }
+  // longest-processing-time order for the persistent queue (ties: list order)
+  std::vector<int64_t> order(n_pairs);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+  std::vector<PairDesc> sorted(n_pairs);
+  for (int64_t s = 0; s < n_pairs; ++s) sorted[s] = desc[order[s]];
+
+  c->t = *t;
+  c->n_pairs = n_pairs;
+  c->flops64 = f64 + (c->precision == PF12_FP64 ? fmix : 0.0);
+  c->flops_mix = fmix;
+  c->bytes_in = bytes;
+  c->max_fwd_ws = max_fwd;
+  c->max_bwd_ws = max_bwd;
+
+  // workspace: one slab per persistent CTA, shared by forward and backward
+  const int bps = std::max(1, pf12::forward_blocks_per_sm(c->precision));
+  const int bps_b = std::max(1, pf12::backward_blocks_per_sm(c->precision));
+  int64_t want = std::min<int64_t>(n_pairs, (int64_t)bps * c->n_sm);
+  int64_t want_b = std::min<int64_t>(n_pairs, (int64_t)bps_b * c->n_sm);
+  want = std::max<int64_t>(want, 1);
+  want_b = std::max<int64_t>(want_b, 1);
+  const int64_t stride = (max_fwd + 31) / 32 * 32;
+  const int64_t stride_b = (max_bwd + 31) / 32 * 32;
+  if (c->ws_cap) {
+    const int64_t fit_f = (int64_t)(c->ws_cap / 8) / std::max<int64_t>(stride, 1);
+    const int64_t fit_b = (int64_t)(c->ws_cap / 8) / std::max<int64_t>(stride_b, 1);
+    if (n_pairs > 0 && (fit_f < 1 || fit_b < 1))
+      return fail(c, PF12_ERR_OOM, "workspace_bytes too small for the largest pair");
+    want = std::min(want, fit_f);
+    want_b = std::min(want_b, fit_b);
+  }
+  c->n_ctas = (int)want;
+  c->n_ctas_bwd = (int)want_b;
+  c->ws_stride = stride;
+  c->ws_stride_bwd = stride_b;
+  const size_t work_doubles = (size_t)std::max(want * stride, want_b * stride_b);
+
+  const size_t n = (size_t)std::max<int64_t>(n_pairs, 1);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_desc, sizeof(PairDesc) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_V, sizeof(double) * (size_t)std::max<int64_t>(t ? t->len_kk : 0, 2));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_epair, sizeof(double) * 3 * n);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_dx, sizeof(double) * 2 * n);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int32_t) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_out3, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, sizeof(int32_t) * 2);
+  if (e == cudaSuccess && n_pairs > 0) e = cudaMalloc(&c->d_work, sizeof(double) * work_doubles);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_pairs(c);
+    return fail(c, e == cudaErrorMemoryAllocation ? PF12_ERR_OOM : PF12_ERR_CUDA,
+                std::string("device allocation: ") + cudaGetErrorString(e));
+  }
+  c->work_bytes = sizeof(double) * work_doubles;
+  PF12_CUDA(c, cudaMemcpyAsync(c->d_desc, sorted.data(), sizeof(PairDesc) * n_pairs,
+                               cudaMemcpyHostToDevice, c->stream));
+  if (t && t->len_kk > 0) PF12_CUDA(c, cudaMemsetAsync(c->d_V, 0, sizeof(double) * t->len_kk, c->stream));
+  PF12_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int32_t) * n, c->stream));
+  PF12_CUDA(c, cudaMemsetAsync(c->d_epair, 0, sizeof(double) * 3 * n, c->stream));
+  PF12_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->uploaded = true;
+  return PF12_OK;
+}
+
+int pf12_fit(pf12_ctx* c) {
+  if (!c) return PF12_ERR_INVALID_ARG;
+  if (!c->uploaded) return fail(c, PF12_ERR_INVALID_ARG, "pf12_fit before pf12_upload_pairs");
+  if (c->n_pairs == 0) {
+    c->fitted = true;
+    return PF12_OK;
+  }
+  if (!c->graph_exec) {
+    // capture on the library's own stream (nothing executes), replay on the caller's
+    PF12_CUDA(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->capture_stream);
+    if (e == cudaSuccess) e = pf12::launch_forward(fwd_params(c), c->precision, c->n_ctas, c->capture_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "capture forward");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "end capture");
+    c->graph = g;
+    PF12_CUDA(c, cudaGraphInstantiate(&c->graph_exec, g, 0));
+  }
+  PF12_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+  PF12_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
+  PF12_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+  c->t_fit = true;
+  c->fitted = true;
+  return PF12_OK;
+}
+
+int pf12_build_v(pf12_ctx* c, double* V_dev) {
+  if (!c || !V_dev) return fail(c, PF12_ERR_INVALID_ARG, "null argument");
+  if (!c->fitted) return fail(c, PF12_ERR_INVALID_ARG, "pf12_build_v before pf12_fit");
+  if (c->n_pairs == 0) return PF12_OK;
+  for (int64_t P = 0; P < c->n_pairs; ++P) {
+    const size_t kk = (size_t)c->pk[P] * c->pk[P];
+    // one copy per pair keeps the caller's padding untouched
+    PF12_CUDA(c, cudaMemcpyAsync(V_dev + c->off_kk[P], c->d_V + c->off_kk[P], kk * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return PF12_OK;
+}
+
+int pf12_energy(pf12_ctx* c, double* e_pair_dev, double* E_host) {
+  if (!c) return PF12_ERR_INVALID_ARG;
+  if (!c->fitted) return fail(c, PF12_ERR_INVALID_ARG, "pf12_energy before pf12_fit");
+  if (c->n_pairs == 0) {
+    if (E_host) *E_host = 0.0;
+    return PF12_OK;
+  }
+  PF12_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
+  PF12_CUDA(c, pf12::launch_energy_total(c->d_epair, c->d_status, c->n_pairs, c->d_out3, c->stream));
+  PF12_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
+  c->t_energy = true;
+  if (e_pair_dev)
+    PF12_CUDA(c, cudaMemcpyAsync(e_pair_dev, c->d_epair, sizeof(double) * 3 * c->n_pairs,
+                                 cudaMemcpyDeviceToDevice, c->stream));
+  if (!E_host) return PF12_OK;
+  double out3[3];
+  PF12_CUDA(c, cudaMemcpyAsync(out3, c->d_out3, sizeof out3, cudaMemcpyDeviceToHost, c->stream));
+  PF12_CUDA(c, cudaStreamSynchronize(c->stream));
+  *E_host = out3[0];
+  if (out3[1] > 0) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "%lld pair(s) failed, first pair %lld", (long long)out3[1], (long long)out3[2]);
+    c->err = buf;
+    int32_t st = 0;
+    PF12_CUDA(c, cudaMemcpy(&st, c->d_status + (int64_t)out3[2], sizeof st, cudaMemcpyDeviceToHost));
+    return st == PF12_PAIR_NOT_SPD ? PF12_ERR_NOT_SPD : PF12_ERR_NONFINITE;
+  }
+  if (!std::isfinite(out3[0])) return fail(c, PF12_ERR_NONFINITE, "total energy not finite");
+  return PF12_OK;
+}
+
+int pf12_backward(pf12_ctx* c, double dE, double* dAgi, double* dAgj, double* dAfi, double* dAfj,
+                  double* dQ, double* dT) {
+  if (!c) return PF12_ERR_INVALID_ARG;
+  if (!c->uploaded) return fail(c, PF12_ERR_INVALID_ARG, "pf12_backward before pf12_upload_pairs");
+  if (c->n_pairs == 0) return PF12_OK;
+  pf12::BwdParams b{};
+  b.f = fwd_params(c);
+  b.f.work = c->d_work;
+  b.f.ws_stride = c->ws_stride_bwd;
+  b.dE = dE;
+  b.dAgi = dAgi;
+  b.dAgj = dAgj;
+  b.dAfi = dAfi;
+  b.dAfj = dAfj;
+  b.dQ = dQ;
+  b.dT = dT;
+  const void* outs[6] = {dAgi, dAgj, dAfi, dAfj, dQ, dT};
+  for (const void* p : outs)
+    if (p && !aligned16(p)) return fail(c, PF12_ERR_INVALID_ARG, "gradient pointer not 16-byte aligned");
+  PF12_CUDA(c, cudaEventRecord(c->ev[4], c->stream));
+  PF12_CUDA(c, cudaMemsetAsync(c->d_counter + 1, 0, sizeof(int32_t), c->stream));
+  PF12_CUDA(c, pf12::launch_backward(b, c->precision, c->n_ctas_bwd, c->stream));
+  PF12_CUDA(c, cudaEventRecord(c->ev[5], c->stream));
+  c->t_bwd = true;
+  return PF12_OK;
+}
+
+int pf12_pair_status(pf12_ctx* c, int32_t* status_host) {
+  if (!c || !status_host) return fail(c, PF12_ERR_INVALID_ARG, "null argument");
+  if (c->n_pairs == 0) return PF12_OK;
+  PF12_CUDA(c, cudaMemcpyAsync(status_host, c->d_status, sizeof(int32_t) * c->n_pairs,
+                               cudaMemcpyDeviceToHost, c->stream));
+  PF12_CUDA(c, cudaStreamSynchronize(c->stream));
+  return PF12_OK;
+}
+
+int pf12_stats(pf12_ctx* c, pf12_stats_t* s) {
+  if (!c || !s) return fail(c, PF12_ERR_INVALID_ARG, "null argument");
+  std::memset(s, 0, sizeof *s);
+  PF12_CUDA(c, cudaStreamSynchronize(c->stream));
+  float ms = 0;
+  if (c->t_fit && cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) s->ms_fit = ms;
+  if (c->t_energy && cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]) == cudaSuccess) s->ms_energy = ms;
+  if (c->t_bwd && cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]) == cudaSuccess) s->ms_backward = ms;
+  cudaGetLastError();
+  s->flops_fp64 = c->flops64;
+  s->flops_mixed = c->flops_mix;
+  s->bytes_in = c->bytes_in;
+  s->n_pairs = c->n_pairs;
+  s->n_ctas = c->n_ctas;
+  s->launches_fit = c->n_pairs > 0 ? 1 : 0;
+  s->tile_config = 0;
+  s->graph_used = c->graph_exec != nullptr;
+  return PF12_OK;
+}
+
+const char* pf12_last_error(const pf12_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void pf12_destroy(pf12_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_pairs(c);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,144 @@
+// Hand-written adjoint of the pair-F12 energy (one persistent fused launch).
+// Each pair's forward intermediates are recomputed, not stored; the two extra
+// FP64 solves give Z^T = (At^f - Ct J_f) J_g^{-1}.  With G_V = dE (alpha T +
+// beta T^T) (E_P = alpha d + beta x):
+//   dT    = dE (alpha V + beta V^T)
+//   H1 = G_V Ct_j,  H2 = G_V^T Ct_i,  H3 = G_V Z_j^T,  H4 = G_V^T Z_i^T   (k x m)
+//   dAf_i = Q H1, dAf_j = Q H2, dAg_i = Q H3, dAg_j = Q H4                (p x m)
+//   dQ    = Af_i H1^T + Af_j H2^T + Ag_i H3^T + Ag_j H4^T                 (p x k)
+// which is the chain rule of V = Q^T K Q, K = A^f_i C_j^T + C_i A^f_j^T -
+// C_i J_f C_j^T, C = A^g J_g^{-1} with J_g, J_f symmetric and held constant.
+#include <cuda_runtime.h>
+
+#include "pf12_device.cuh"
+#include "pf12_internal.h"
+
+namespace pf12 {
+
+template <typename TC>
+__device__ void pair_backward(const BwdParams& b, const PairDesc& pd, double* ws, GemmSmem& gs,
+                              CholSmem& cs) {
+  const FwdParams& prm = b.f;
+  const int tid = threadIdx.x;
+  const int p = pd.p, k = pd.k, m = pd.m;
+  const int64_t ld = (m + 3) / 4 * 4;
+  const int64_t ldk = (k + 3) / 4 * 4;
+  double* M = ws;                                // m + 2k rows
+  double* F = M + (int64_t)(m + 2 * k) * ld;     // 2k rows
+  double* R = F + 2 * (int64_t)k * ld;           // 2k rows
+  double* GV = R + 2 * (int64_t)k * ld;          // k x ldk
+  double* Vl = GV + (int64_t)k * ldk;            // k x ldk
+  const double* Jg = prm.Jg + pd.off_mm;
+  const double* Jf = prm.Jf + pd.off_mm;
+  const double* Q = prm.Q + pd.off_pk;
+  const double* T = prm.T + pd.off_kk;
+  const double* Agi = prm.Agi + pd.off_pm;
+  const double* Agj = prm.Agj + pd.off_pm;
+  const double* Afi = prm.Afi + pd.off_pm;
+  const double* Afj = prm.Afj + pd.off_pm;
+
+  for (int r = tid >> 5; r < m; r += kThreads / 32)
+    for (int c = tid & 31; c < m; c += 32) M[(int64_t)r * ld + c] = Jg[(int64_t)r * m + c];
+  cta_gemm<TC, true, false>(k, m, p, Q, k, Agi, m, M + (int64_t)m * ld, ld, 1.0, false, gs);
+  cta_gemm<TC, true, false>(k, m, p, Q, k, Agj, m, M + (int64_t)(m + k) * ld, ld, 1.0, false, gs);
+  cta_gemm<TC, true, false>(k, m, p, Q, k, Afi, m, F, ld, 1.0, false, gs);
+  cta_gemm<TC, true, false>(k, m, p, Q, k, Afj, m, F + (int64_t)k * ld, ld, 1.0, false, gs);
+
+  if (!chol_augmented(M, ld, m, m + 2 * k, cs, gs)) {
+    if (tid == 0) prm.status[pd.pair] = 1;
+    return;
+  }
+  double* Ci = M + (int64_t)m * ld;
+  double* Cj = M + (int64_t)(m + k) * ld;
+  solve_right_lower(M, ld, m, Ci, ld, 2 * k, cs, gs);
+
+  // R = At^f - Ct J_f  (both x at once: Ct_i, Ct_j are consecutive rows)
+  for (int64_t e = tid; e < 2 * (int64_t)k * ld; e += kThreads) R[e] = F[e];
+  __syncthreads();
+  cta_gemm<TC, false, false>(2 * k, m, m, Ci, ld, Jf, m, R, ld, -1.0, true, gs);
+
+  // V = R_i Ct_j^T + Ct_i At^f_j^T
+  for (int r0 = 0; r0 < k; r0 += kTile)
+    for (int c0 = 0; c0 < k; c0 += kTile) {
+      cta_gemm_tile<TC, false, true>(k, k, m, R, ld, Cj, ld, Vl, ldk, r0, c0, 1.0, false, gs);
+      cta_gemm_tile<TC, false, true>(k, k, m, Ci, ld, F + (int64_t)k * ld, ld, Vl, ldk, r0, c0, 1.0,
+                                     true, gs);
+    }
+  __syncthreads();
+
+  const double alpha = 3.0 * pd.n_ab / 8.0 + (pd.n_aa + pd.n_bb) / 4.0;
+  const double beta = pd.n_ab / 8.0 - (pd.n_aa + pd.n_bb) / 4.0;
+  double* dT = b.dT ? b.dT + pd.off_kk : nullptr;
+  for (int e = tid; e < k * k; e += kThreads) {
+    const int a = e / k, c = e - a * k;
+    GV[a * ldk + c] = b.dE * (alpha * T[a * k + c] + beta * T[c * k + a]);
+    if (dT) dT[e] = b.dE * (alpha * Vl[a * ldk + c] + beta * Vl[c * ldk + a]);
+  }
+  __syncthreads();
+
+  // Z^T = R J_g^{-1}: forward then backward FP64 solve on the 2k rows of R
+  solve_right_lowerT(M, ld, m, R, ld, 2 * k, cs, gs);
+  solve_right_lower(M, ld, m, R, ld, 2 * k, cs, gs);
+  double* Zi = R;
+  double* Zj = R + (int64_t)k * ld;
+
+  double* H1 = F;
+  double* H2 = F + (int64_t)k * ld;
+  double* dQ = b.dQ ? b.dQ + pd.off_pk : nullptr;
+  // H1 = G_V Ct_j, H2 = G_V^T Ct_i
+  cta_gemm<TC, false, false>(k, m, k, GV, ldk, Cj, ld, H1, ld, 1.0, false, gs);
+  cta_gemm<TC, true, false>(k, m, k, GV, ldk, Ci, ld, H2, ld, 1.0, false, gs);
+  if (b.dAfi) cta_gemm<TC, false, false>(p, m, k, Q, k, H1, ld, b.dAfi + pd.off_pm, m, 1.0, false, gs);
+  if (b.dAfj) cta_gemm<TC, false, false>(p, m, k, Q, k, H2, ld, b.dAfj + pd.off_pm, m, 1.0, false, gs);
+  if (dQ) {
+    cta_gemm<TC, false, true>(p, k, m, Afi, m, H1, ld, dQ, k, 1.0, false, gs);
+    cta_gemm<TC, false, true>(p, k, m, Afj, m, H2, ld, dQ, k, 1.0, true, gs);
+  }
+  // H3 = G_V Z_j^T, H4 = G_V^T Z_i^T
+  cta_gemm<TC, false, false>(k, m, k, GV, ldk, Zj, ld, H1, ld, 1.0, false, gs);
+  cta_gemm<TC, true, false>(k, m, k, GV, ldk, Zi, ld, H2, ld, 1.0, false, gs);
+  if (b.dAgi) cta_gemm<TC, false, false>(p, m, k, Q, k, H1, ld, b.dAgi + pd.off_pm, m, 1.0, false, gs);
+  if (b.dAgj) cta_gemm<TC, false, false>(p, m, k, Q, k, H2, ld, b.dAgj + pd.off_pm, m, 1.0, false, gs);
+  if (dQ) {
+    cta_gemm<TC, false, true>(p, k, m, Agi, m, H1, ld, dQ, k, 1.0, true, gs);
+    cta_gemm<TC, false, true>(p, k, m, Agj, m, H2, ld, dQ, k, 1.0, true, gs);
+  }
+  if (tid == 0) prm.status[pd.pair] = 0;
+}
+
+template <typename TC>
+__global__ void __launch_bounds__(kThreads, 2) pair_backward_kernel(BwdParams b) {
+  __shared__ GemmSmem gs;
+  __shared__ CholSmem cs;
+  __shared__ long long s_slot;
+  double* ws = b.f.work + (int64_t)blockIdx.x * b.f.ws_stride;
+  for (;;) {
+    if (threadIdx.x == 0) s_slot = atomicAdd(b.f.counter + 1, 1);
+    __syncthreads();
+    const long long slot = s_slot;
+    __syncthreads();
+    if (slot >= b.f.n_pairs) break;
+    const PairDesc pd = b.f.desc[slot];
+    pair_backward<TC>(b, pd, ws, gs, cs);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_backward(const BwdParams& prm, int precision, int n_ctas, cudaStream_t s) {
+  if (precision == 0)
+    pair_backward_kernel<double><<<n_ctas, kThreads, 0, s>>>(prm);
+  else
+    pair_backward_kernel<float><<<n_ctas, kThreads, 0, s>>>(prm);
+  return cudaGetLastError();
+}
+
+int backward_blocks_per_sm(int precision) {
+  int n = 0;
+  if (precision == 0)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_backward_kernel<double>, kThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_backward_kernel<float>, kThreads, 0);
+  return n;
+}
+
+}  // namespace pf12

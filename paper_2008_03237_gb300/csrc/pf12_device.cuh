@@ -1,0 +1,329 @@
+// Device building blocks of the pair-F12 kernels: a CTA-wide GEMM tile, the
+// FP64 right-looking Cholesky of an augmented matrix (factor + forward solve in
+// one sweep), the FP64 backward solve, and a fixed-order block reduction.
+//
+// Every routine is executed by all kThreads threads of one CTA and works on a
+// single pair's workspace; none waits on another CTA.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pf12_internal.h"
+
+namespace pf12 {
+
+struct __align__(16) GemmSmem {
+  double buf[2 * kBK * (kTile + 1)];  // A and B tiles (as double or as float)
+};
+
+struct __align__(16) CholSmem {
+  double d[kNB][kNB + 1];  // diagonal block of L
+  double inv[kNB];         // 1 / L_tt
+  int ok;
+};
+
+// ---------------------------------------------------------------------------
+// CTA GEMM tile:  C[r, c] = (acc ? C[r, c] : 0) + alpha * sum_{t<K} A(r, t) B(t, c)
+// for r0 <= r < min(r0 + 64, M), c0 <= c < min(c0 + 64, N), where
+//   A(r, t) = TA ? A[t * lda + r] : A[r * lda + t]
+//   B(t, c) = TB ? B[c * ldb + t] : B[t * ldb + c].
+// TC is the product type: double (FP64 FMAs) or float (FP32 FMAs over 32-wide
+// K chunks, each chunk's partial sum added to an FP64 accumulator).  Operands
+// may alias C's array as long as the tile's own C entries are not read as A/B.
+// Ends with all threads synchronised; C stores happen after the final barrier
+// and are read back only by the thread that wrote them.
+template <typename TC, bool TA, bool TB>
+__device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double* A, int64_t lda,
+                                              const double* B, int64_t ldb, double* C,
+                                              int64_t ldc, int r0, int c0, double alpha,
+                                              bool accumulate, GemmSmem& sm) {
+  TC (*as)[kTile + 1] = reinterpret_cast<TC (*)[kTile + 1]>(sm.buf);
+  TC (*bs)[kTile + 1] = reinterpret_cast<TC (*)[kTile + 1]>(sm.buf + kBK * (kTile + 1));
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  double accd[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) accd[i][j] = 0.0;
+
+  for (int k0 = 0; k0 < K; k0 += kBK) {
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      int r, t;
+      if (!TA) { t = tid & 31; r = (tid >> 5) + 8 * s; }
+      else     { r = tid & 63; t = (tid >> 6) + 4 * s; }
+      const int gr = r0 + r, gt = k0 + t;
+      double v = 0.0;
+      if (gr < M && gt < K) v = TA ? A[(int64_t)gt * lda + gr] : A[(int64_t)gr * lda + gt];
+      as[t][r] = (TC)v;
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      int c, t;
+      if (TB) { t = tid & 31; c = (tid >> 5) + 8 * s; }
+      else    { c = tid & 63; t = (tid >> 6) + 4 * s; }
+      const int gc = c0 + c, gt = k0 + t;
+      double v = 0.0;
+      if (gc < N && gt < K) v = TB ? B[(int64_t)gc * ldb + gt] : B[(int64_t)gt * ldb + gc];
+      bs[t][c] = (TC)v;
+    }
+    __syncthreads();
+    const int kn = min(kBK, K - k0);
+    if constexpr (sizeof(TC) == sizeof(double)) {
+      if (kn == kBK) {
+#pragma unroll 8
+        for (int kk = 0; kk < kBK; ++kk) {
+          double a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = as[kk][ty + 16 * i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = bs[kk][tx + 16 * j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) accd[i][j] = fma(a[i], b[j], accd[i][j]);
+        }
+      } else {
+        for (int kk = 0; kk < kn; ++kk) {
+          double a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = as[kk][ty + 16 * i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = bs[kk][tx + 16 * j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) accd[i][j] = fma(a[i], b[j], accd[i][j]);
+        }
+      }
+    } else {
+      float acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+      for (int kk = 0; kk < kn; ++kk) {
+        float a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = as[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) accd[i][j] += (double)acc[i][j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty + 16 * i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + tx + 16 * j;
+      if (c >= N) continue;
+      double* pc = C + (int64_t)r * ldc + c;
+      *pc = accumulate ? fma(alpha, accd[i][j], *pc) : alpha * accd[i][j];
+    }
+  }
+}
+
+// Whole-matrix product over all 64 x 64 output tiles of an M x N result.
+template <typename TC, bool TA, bool TB>
+__device__ __forceinline__ void cta_gemm(int M, int N, int K, const double* A, int64_t lda,
+                                         const double* B, int64_t ldb, double* C, int64_t ldc,
+                                         double alpha, bool accumulate, GemmSmem& sm) {
+  for (int r0 = 0; r0 < M; r0 += kTile)
+    for (int c0 = 0; c0 < N; c0 += kTile)
+      cta_gemm_tile<TC, TA, TB>(M, N, K, A, lda, B, ldb, C, ldc, r0, c0, alpha, accumulate, sm);
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Right-looking blocked Cholesky of the leading m x m block of M (row-major,
+// leading dimension ld, lower triangle used), FP64, extended to the extra rows
+// [m, rows): on return M[0:m, 0:m] holds L (lower) and M[m:rows, 0:m] holds
+// M[m:rows] L^{-T}, i.e. the forward solve rides along the factorisation as
+// extra rows of every panel solve and trailing update.  Entries above the
+// diagonal are scratch.  Returns false on every thread when a pivot is not
+// positive and finite (J_g not SPD).
+__device__ __forceinline__ bool chol_augmented(double* M, int64_t ld, int m, int rows,
+                                               CholSmem& cs, GemmSmem& gs) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int kb = 0; kb < m; kb += kNB) {
+    const int nb = min(kNB, m - kb);
+    for (int e = tid; e < nb * nb; e += kThreads) {
+      const int r = e / nb, c = e - r * nb;
+      cs.d[r][c] = (c <= r) ? M[(int64_t)(kb + r) * ld + kb + c] : 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int ok = 1;
+      for (int j = 0; j < nb; ++j) {
+        const double djj = cs.d[j][j];
+        if (!(djj > 0.0) || !isfinite(djj)) ok = 0;
+        const double l = sqrt(djj);
+        const double inv = 1.0 / l;
+        __syncwarp();
+        if (lane == j) { cs.d[j][j] = l; cs.inv[j] = inv; }
+        if (lane > j && lane < nb) cs.d[lane][j] *= inv;
+        __syncwarp();
+        if (lane > j && lane < nb) {
+          const double lrj = cs.d[lane][j];
+          for (int c = j + 1; c <= lane; ++c) cs.d[lane][c] = fma(-lrj, cs.d[c][j], cs.d[lane][c]);
+        }
+        __syncwarp();
+      }
+      if (lane == 0) cs.ok = ok;
+    }
+    __syncthreads();
+    if (!cs.ok) return false;
+    for (int e = tid; e < nb * nb; e += kThreads) {
+      const int r = e / nb, c = e - r * nb;
+      if (c <= r) M[(int64_t)(kb + r) * ld + kb + c] = cs.d[r][c];
+    }
+    // panel solve: rows below the diagonal block, X L_kk^T = A_panel
+    for (int r = kb + nb + tid; r < rows; r += kThreads) {
+      double* row = M + (int64_t)r * ld + kb;
+      double x[kNB];
+#pragma unroll
+      for (int t = 0; t < kNB; ++t) x[t] = (t < nb) ? row[t] : 0.0;
+#pragma unroll
+      for (int t = 0; t < kNB; ++t) {
+        if (t < nb) {
+          double s = x[t];
+#pragma unroll
+          for (int q = 0; q < t; ++q) s = fma(-x[q], cs.d[t][q], s);
+          x[t] = s * cs.inv[t];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kNB; ++t)
+        if (t < nb) row[t] = x[t];
+    }
+    __syncthreads();
+    // trailing update of the lower part (and of every extra row)
+    const int rb = kb + nb;
+    for (int R = rb; R < rows; R += kTile)
+      for (int C = rb; C < m && C < R + kTile; C += kTile)
+        cta_gemm_tile<double, false, true>(rows, m, nb, M + kb, ld, M + kb, ld, M, ld, R, C, -1.0,
+                                           true, gs);
+    __syncthreads();
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Backward solve Y <- Y L^{-1} (FP64) for nrows rows of Y (leading dimension
+// ldy) and the lower-triangular m x m factor L (leading dimension ld):
+// column blocks from the right, each a small in-register triangular solve
+// followed by a rank-nb update of the columns to its left.
+__device__ __forceinline__ void solve_right_lower(const double* L, int64_t ld, int m, double* Y,
+                                                  int64_t ldy, int nrows, CholSmem& cs,
+                                                  GemmSmem& gs) {
+  const int tid = threadIdx.x;
+  const int nblk = (m + kNB - 1) / kNB;
+  for (int cb = nblk - 1; cb >= 0; --cb) {
+    const int c0 = cb * kNB, nb = min(kNB, m - c0);
+    for (int e = tid; e < nb * nb; e += kThreads) {
+      const int r = e / nb, c = e - r * nb;
+      cs.d[r][c] = (c <= r) ? L[(int64_t)(c0 + r) * ld + c0 + c] : 0.0;
+    }
+    __syncthreads();
+    if (tid < nb) cs.inv[tid] = 1.0 / cs.d[tid][tid];
+    __syncthreads();
+    for (int r = tid; r < nrows; r += kThreads) {
+      double* row = Y + (int64_t)r * ldy + c0;
+      double x[kNB];
+#pragma unroll
+      for (int t = 0; t < kNB; ++t) x[t] = (t < nb) ? row[t] : 0.0;
+#pragma unroll
+      for (int t = kNB - 1; t >= 0; --t) {
+        if (t < nb) {
+          double s = x[t];
+#pragma unroll
+          for (int q = t + 1; q < kNB; ++q)
+            if (q < nb) s = fma(-x[q], cs.d[q][t], s);
+          x[t] = s * cs.inv[t];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kNB; ++t)
+        if (t < nb) row[t] = x[t];
+    }
+    __syncthreads();
+    if (c0 > 0)
+      cta_gemm<double, false, false>(nrows, c0, nb, Y + c0, ldy, L + (int64_t)c0 * ld, ld, Y, ldy,
+                                     -1.0, true, gs);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward solve Y <- Y L^{-T} (FP64) for nrows rows of Y: column blocks from the
+// left, each an in-register triangular solve followed by a rank-nb update of
+// the columns to its right.
+__device__ __forceinline__ void solve_right_lowerT(const double* L, int64_t ld, int m, double* Y,
+                                                   int64_t ldy, int nrows, CholSmem& cs,
+                                                   GemmSmem& gs) {
+  const int tid = threadIdx.x;
+  for (int kb = 0; kb < m; kb += kNB) {
+    const int nb = min(kNB, m - kb);
+    for (int e = tid; e < nb * nb; e += kThreads) {
+      const int r = e / nb, c = e - r * nb;
+      cs.d[r][c] = (c <= r) ? L[(int64_t)(kb + r) * ld + kb + c] : 0.0;
+    }
+    __syncthreads();
+    if (tid < nb) cs.inv[tid] = 1.0 / cs.d[tid][tid];
+    __syncthreads();
+    for (int r = tid; r < nrows; r += kThreads) {
+      double* row = Y + (int64_t)r * ldy + kb;
+      double x[kNB];
+#pragma unroll
+      for (int t = 0; t < kNB; ++t) x[t] = (t < nb) ? row[t] : 0.0;
+#pragma unroll
+      for (int t = 0; t < kNB; ++t) {
+        if (t < nb) {
+          double s = x[t];
+#pragma unroll
+          for (int q = 0; q < t; ++q) s = fma(-x[q], cs.d[t][q], s);
+          x[t] = s * cs.inv[t];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kNB; ++t)
+        if (t < nb) row[t] = x[t];
+    }
+    __syncthreads();
+    if (kb + nb < m)
+      cta_gemm<double, false, true>(nrows, m - kb - nb, nb, Y + kb, ldy,
+                                    L + (int64_t)(kb + nb) * ld + kb, ld, Y + kb + nb, ldy, -1.0,
+                                    true, gs);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-order CTA sum of two per-thread values (deterministic for a fixed
+// kThreads): butterfly within each warp, then warps in index order.
+__device__ __forceinline__ void cta_sum2(double& a, double& b, double (*red)[kThreads / 32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) { red[0][warp] = a; red[1][warp] = b; }
+  __syncthreads();
+  double sa = 0.0, sb = 0.0;
+  for (int w = 0; w < kThreads / 32; ++w) { sa += red[0][w]; sb += red[1][w]; }
+  __syncthreads();
+  a = sa;
+  b = sb;
+}
+
+}  // namespace pf12

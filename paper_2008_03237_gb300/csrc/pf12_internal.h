@@ -1,0 +1,63 @@
+// Internal declarations shared by the host API and the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pf12 {
+
+constexpr int kThreads = 256;   // threads per CTA of every pair kernel
+constexpr int kTile = 64;       // output tile edge of the CTA GEMM
+constexpr int kBK = 32;         // K chunk of the CTA GEMM
+constexpr int kNB = 32;         // Cholesky / solve panel width
+constexpr int kMaxAux = 4096;   // m limit (workspace and index arithmetic in int32)
+constexpr int kMaxPno = 256;    // k limit
+
+// One entry per pair, in the persistent kernel's (cost-sorted) order.
+struct PairDesc {
+  int64_t off_pm, off_mm, off_pk, off_kk;  // element offsets into the packed inputs
+  int32_t p, k, m, pair;                   // sizes and the pair's index in the caller's list
+  float w_alpha, w_beta;                   // E_P = w_alpha d + w_beta x (as FP64 below)
+  int8_t n_ab, n_aa, n_bb, pad;            // spin-case multiplicities
+};
+
+struct FwdParams {
+  const double *Agi, *Agj, *Afi, *Afj, *Jg, *Jf, *Q, *T;
+  const PairDesc* desc;
+  int64_t n_pairs;
+  double* V;          // ctx-owned, same layout as T
+  double* e_pair;     // n_pairs x 3, indexed by the caller's pair index
+  double* dx;         // n_pairs x 2 (d, x), caller's index
+  int32_t* status;    // n_pairs, caller's index
+  double* work;       // n_ctas * ws_stride doubles
+  int64_t ws_stride;  // doubles per CTA
+  int32_t* counter;   // work-queue head, zeroed before each launch
+};
+
+struct BwdParams {
+  FwdParams f;
+  double dE;
+  double *dAgi, *dAgj, *dAfi, *dAfj, *dQ, *dT;
+};
+
+// per-CTA workspace (doubles) for a pair of sizes (p, k, m), forward / backward
+inline int64_t ld_of(int m) { return (int64_t)((m + 3) / 4 * 4); }
+inline int64_t fwd_ws(int p, int k, int m) {
+  int64_t ld = ld_of(m);
+  return (int64_t)(m + 2 * k) * ld + 2 * (int64_t)k * ld + 64;
+}
+inline int64_t bwd_ws(int p, int k, int m) {
+  int64_t ld = ld_of(m);
+  int64_t ldk = (k + 3) / 4 * 4;
+  // M = [J_g -> L; Ct_i; Ct_j] (m + 2k rows), F (2k rows: At^f, then H),
+  // R (2k rows: At^f - Ct J_f, then Z^T), G_V and V (k x k each)
+  return (int64_t)(m + 6 * k) * ld + 2 * (int64_t)k * ldk + 64;
+}
+
+cudaError_t launch_forward(const FwdParams& prm, int precision, int n_ctas, cudaStream_t s);
+cudaError_t launch_backward(const BwdParams& prm, int precision, int n_ctas, cudaStream_t s);
+cudaError_t launch_energy_total(const double* e_pair, const int32_t* status, int64_t n_pairs,
+                                double* out3, cudaStream_t s);
+int forward_blocks_per_sm(int precision);
+int backward_blocks_per_sm(int precision);
+
+}  // namespace pf12

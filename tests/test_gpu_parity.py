@@ -1,0 +1,195 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: FP64 mode within 1e-10 Eh per pair; mixed mode within 1 uEh in total
+after the chemical-scale normalisation (reading G1), gradients within 1e-9
+(FP64) of the oracle's, relative to the largest entry of each block.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synthetic as S
+from gpu_helpers import grad_blocks, normalised_error, run, sized_workload, upload_host
+
+pytestmark = pytest.mark.gpu
+
+# sizes that span several 64-wide tiles and 32-wide panels with ragged tails,
+# plus the degenerate ends (k = 1, m = 1, k = p)
+EDGE_SIZES = [(1, 1, 1), (7, 7, 3), (5, 2, 33), (65, 64, 65), (130, 70, 129), (200, 1, 257),
+              (33, 33, 31), (90, 41, 190), (64, 64, 64), (128, 96, 300)]
+
+
+def _mini():
+    return S.custom(5, 2, None, (40, 150), ("uniform", 1, 90), (30, 230), name="mini-ragged")
+
+
+def _edge():
+    return sized_workload(EDGE_SIZES, kinds=[0] * 8 + [1] * 3, diag_every=3, name="edge-sizes")
+
+
+@pytest.fixture(scope="module")
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _check_fp64(wl, r, ref):
+    err = np.abs(r["e_pair"] - ref["e_pair"]).max()
+    assert err <= 1e-10, f"max |de_pair| = {err}"
+    for P in range(wl.n_pairs):
+        scale = max(np.abs(ref["V"][P]).max(), 1e-300)
+        assert np.abs(r["V"][P] - ref["V"][P]).max() <= 1e-11 * scale, P
+    assert abs(r["E"] - ref["E"]) <= 1e-10 * max(1.0, abs(ref["E"]))
+
+
+@pytest.mark.parametrize("make", [S.tiny, _mini, _edge])
+def test_forward_fp64(built, make):
+    wl = make()
+    ref = O.run(wl, want_V=True)
+    r = run(wl, "fp64")
+    _check_fp64(wl, r, ref)
+
+
+@pytest.mark.parametrize("make", [S.tiny, _mini, _edge])
+def test_forward_mixed(built, make):
+    wl = make()
+    ref = O.run(wl)
+    r = run(wl, "mixed_fp32", want_V=False)
+    rel = np.abs(r["e_pair"] - ref["e_pair"]).max() / np.abs(ref["e_pair"]).max()
+    assert rel <= 1e-5, rel
+    err = normalised_error(r["E"] - ref["E"], ref["sum_abs"], wl.n_orb)
+    assert err <= 1e-6, f"normalised total error {err} Eh"
+
+
+def test_device_generator_bitwise(built):
+    from synthetic import device
+    wl = _edge()
+    host, lay = S.packed_inputs(wl)
+    t, lay2 = device.allocate(wl)
+    device.fill(wl, t, lay2)
+    for n, v in host.items():
+        assert np.array_equal(t[n].cpu().numpy()[:v.size], v), n
+
+
+def test_empty_pair_list(built):
+    wl = sized_workload([])
+    r = run(wl, "fp64", want_V=False)
+    assert r["E"] == 0.0 and r["e_pair"].shape == (0, 3)
+
+
+def test_graph_replay_is_deterministic(built):
+    wl = _mini()
+    r = run(wl, "fp64", want_V=False)
+    eng = r["eng"]
+    E1, e1 = eng.energy()
+    e1 = e1.cpu().numpy().copy()
+    for _ in range(2):
+        eng.fit()
+        E2, e2 = eng.energy()
+        assert E2 == E1
+        assert np.array_equal(e2.cpu().numpy(), e1)
+    assert eng.stats()["graph_used"] == 1
+
+
+def test_not_spd_pair_is_reported(built):
+    import paper_2008_03237_gb300 as pf
+    wl = S.tiny()
+    host, lay = S.packed_inputs(wl)
+    bad = 5
+    m = int(wl.n_aux[bad])
+    o = lay["off_mm"][bad]
+    J = host["Jg"][o:o + m * m].reshape(m, m)
+    J -= 20.0 * np.eye(m)
+    t, lay = upload_host(wl, (host, lay))
+    eng = pf.PairF12("fp64")
+    eng.upload_pairs(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
+    eng.fit()
+    with pytest.raises(pf.Pf12Error) as ei:
+        eng.energy()
+    assert ei.value.code == -2
+    st = eng.pair_status()
+    assert st[bad] == 1 and (np.delete(st, bad) == 0).all()
+    _, e_pair = eng.energy(check=False)
+    e = e_pair.cpu().numpy()
+    ref = O.run(wl, pairs=[P for P in range(wl.n_pairs) if P != bad])
+    assert np.isnan(e[bad]).all()
+    assert np.abs(np.delete(e, bad, axis=0) - ref["e_pair"]).max() <= 1e-10
+
+
+def test_invalid_arguments(built):
+    import paper_2008_03237_gb300 as pf
+    wl = S.tiny()
+    t, lay = upload_host(wl)
+    eng = pf.PairF12("fp64")
+    base = dict(n_orb=wl.n_orb, orb_kind=wl.orb_kind, pi=wl.pi, pj=wl.pj, n_pao=wl.n_pao,
+                n_pno=wl.n_pno, n_aux=wl.n_aux, tensors=t, offsets=lay)
+    bad_cases = [
+        dict(pi=wl.pj, pj=wl.pi),                                   # i > j
+        dict(n_pno=wl.n_pao + 1),                                   # k > p
+        dict(offsets=dict(lay, off_pm=lay["off_pm"] + 1)),          # misaligned offset
+        dict(offsets=dict(lay, off_mm=lay["off_mm"] + 10**9)),      # block outside buffer
+        dict(orb_kind=np.full(wl.n_orb, 3, np.int8)),               # bad orbital kind
+    ]
+    for case in bad_cases:
+        args = dict(base, **case)
+        with pytest.raises(pf.Pf12Error) as ei:
+            eng.upload_pairs(**args)
+        assert ei.value.code == -1
+    eng.upload_pairs(**base)
+    eng.fit()
+    assert np.isfinite(eng.energy()[0])
+
+
+@pytest.mark.parametrize("make", [S.tiny, _edge])
+def test_backward_fp64(built, make):
+    wl = make()
+    ref = O.run(wl, want_grad=True, dE=0.7)
+    r = run(wl, "fp64", want_V=False, want_grad=True, dE=0.7)
+    for P in range(wl.n_pairs):
+        got = grad_blocks(wl, r["lay"], r["grads"], P)
+        for n, want in ref["grads"][P].items():
+            scale = max(np.abs(want).max(), 1e-300)
+            assert np.abs(got[n] - want).max() <= 1e-9 * scale, (P, n)
+
+
+def test_backward_mixed(built):
+    wl = _mini()
+    ref = O.run(wl, want_grad=True)
+    r = run(wl, "mixed_fp32", want_V=False, want_grad=True)
+    for P in range(wl.n_pairs):
+        got = grad_blocks(wl, r["lay"], r["grads"], P)
+        for n, want in ref["grads"][P].items():
+            scale = max(np.abs(want).max(), 1e-300)
+            assert np.abs(got[n] - want).max() <= 2e-5 * scale, (P, n)
+
+
+def test_autograd_function_and_finite_differences(built):
+    import paper_2008_03237_gb300 as pf
+    wl = S.custom(3, 1, None, (20, 40), ("uniform", 3, 12), (20, 70), name="autograd")
+    t, lay = upload_host(wl)
+    meta = dict(lay, n_orb=wl.n_orb, orb_kind=wl.orb_kind, pi=wl.pi, pj=wl.pj, n_pao=wl.n_pao,
+                n_pno=wl.n_pno, n_aux=wl.n_aux, precision="fp64")
+    leaves = {n: t[n].clone().requires_grad_(n not in ("Jg", "Jf"))
+              for n in ("Agi", "Agj", "Afi", "Afj", "Jg", "Jf", "Q", "T")}
+    E = pf.pair_f12_energy(*[leaves[n] for n in ("Agi", "Agj", "Afi", "Afj", "Jg", "Jf", "Q", "T")],
+                           meta)
+    E.backward()
+    ref = O.run(wl)
+    assert abs(E.item() - ref["E"]) <= 1e-10
+    rng = np.random.default_rng(7)
+    h = 1e-5
+    for n in ("Agi", "Agj", "Afi", "Afj", "Q", "T"):
+        g = leaves[n].grad
+        for _ in range(5):
+            d = torch.from_numpy(rng.standard_normal(t[n].numel())).cuda()
+            d /= d.norm()
+            ep = pf.pair_f12_energy(*[(t[x] + h * d) if x == n else t[x]
+                                      for x in ("Agi", "Agj", "Afi", "Afj", "Jg", "Jf", "Q", "T")],
+                                    meta).item()
+            em = pf.pair_f12_energy(*[(t[x] - h * d) if x == n else t[x]
+                                      for x in ("Agi", "Agj", "Afi", "Afj", "Jg", "Jf", "Q", "T")],
+                                    meta).item()
+            fd = (ep - em) / (2 * h)
+            an = float((g * d).sum())
+            assert abs(fd - an) <= 1e-7 * max(abs(an), float(g.norm()) * 1e-3) + 1e-12, (n, fd, an)
