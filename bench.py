@@ -1,0 +1,425 @@
+"""Throughput of the pair-F12 path on GB300 (one JSON line on rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload c160h321] [--precision mixed_fp32] [--max-pairs N]
+
+A step is one pass of the whole path over the workload's pair list: the fused
+persistent forward launch (projections, FP64 Cholesky + solves, robust-fit V,
+pair contractions) and the fixed-order FP64 energy total.  Inputs are drawn on
+the device before timing (synthetic, seeded) and stay resident in HBM; they
+total ~177 GB for the C160H321-shaped chain, far above the 129 MB L2, so no
+L2 flush is needed between steps.
+
+Also reported: the same step in plain FP64 mode, the error of the mixed-precision
+energies against it, an end-to-end figure through the public API from pinned
+host buffers, the roofline of the fused kernel, SM clocks sampled during the
+timed region, and the FP64 CPU oracle timed on a bounded sample on the host
+cores (--impl reference times that oracle as the reference arm).
+
+Multi-GPU (torchrun): every rank runs an independent copy of the workload
+(its own seed), so per-GPU work is fixed (weak scaling) and there is no
+data-path collective; value = all ranks' pairs / the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "F12 pairs/s & TFLOP/s, mixed-prec vs plain FP64 on 1 GB300 at ≤1 µEh error"
+FP64_PEAK_TFLOPS = 1.25     # nominal GB300 dense FP64 (DFMA), 152 SMs x 4 flop/clk x 2.07 GHz
+CHEM_SCALE_PER_ORB = 4.8e-3  # Eh per orbital (C160H322 F12 correction / valence orbitals)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c160h321")
+    ap.add_argument("--precision", default="mixed_fp32", choices=["mixed_fp32", "fp64"])
+    ap.add_argument("--max-pairs", type=int, default=0, help="deterministic subset (profiling)")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def make_workload(name, max_pairs, rank=0):
+    import synthetic as S
+    wl = S.WORKLOADS[name]()
+    if rank:
+        wl.seed += 1000 * rank
+    if max_pairs and max_pairs < wl.n_pairs:
+        idx = np.linspace(0, wl.n_pairs - 1, max_pairs).round().astype(np.int64)
+        wl = wl.subset(np.unique(idx), name=f"{wl.name}[{max_pairs} pairs]")
+    return wl
+
+
+def flops_bytes(wl):
+    p, k, m = (wl.n_pao.astype(float), wl.n_pno.astype(float), wl.n_aux.astype(float))
+    f64 = float((m ** 3 / 3 + 4 * k * m * m).sum())
+    fmix = float((8 * p * k * m + 2 * k * m * m + 4 * k * k * m).sum())
+    byts = float((8 * (4 * p * m + 2 * m * m + p * k + k * k)).sum())
+    return f64, fmix, byts
+
+
+# --------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = np.array([num(r[1]) for r in rows])
+        mx = np.nanmax([num(r[2]) for r in rows])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": float(mx), "reasons": reasons,
+                "samples": len(rows), "power_w_max": float(np.nanmax([num(r[3]) for r in rows]))}
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+
+def cpu_oracle_rate(wl, budget_s, threads=None):
+    """FP64 CPU oracle (as it stands) on a deterministic sample of wl's pairs:
+    inputs drawn first, only the oracle's evaluation timed.  Runs in a child
+    process with an explicit BLAS thread count.  Returns (pairs/s, threads, sample)."""
+    threads = threads or os.cpu_count() or 1
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=str(threads), OMP_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads))
+    code = f"""
+import sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import oracle, synthetic as S
+from bench import make_workload
+wl = make_workload({wl.meta.get('bench_name', 'c160h321')!r}, {int(wl.meta.get('bench_max', 0))})
+n = wl.n_pairs
+order = np.random.default_rng(12345).permutation(n)
+done, t_used, pairs = 0, 0.0, []
+cache = {{}}
+for P in order:
+    P = int(P)
+    cache[P] = S.pair_inputs(wl, P)
+    t0 = time.perf_counter()
+    oracle.run(wl, pairs=[P], inputs=lambda q: cache[q])
+    t_used += time.perf_counter() - t0
+    del cache[P]
+    done += 1
+    pairs.append(P)
+    if t_used >= {budget_s}:
+        break
+print(json.dumps(dict(rate=done / t_used, done=done, seconds=t_used)))
+"""
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("cpu oracle failed: " + r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return out["rate"], threads, (f"{out['done']} pairs of {wl.name} drawn by a fixed permutation "
+                                  f"(seed 12345), {out['seconds']:.1f} s of oracle time")
+
+
+# --------------------------------------------------------------------------- our arm
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    import paper_2008_03237_gb300 as pf
+    from synthetic import device
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+        __graft_entry__.build()
+    wl = make_workload(args.workload, args.max_pairs, rank)
+    wl.meta["bench_name"] = args.workload
+    wl.meta["bench_max"] = args.max_pairs
+    f64, fmix, byts = flops_bytes(wl)
+    t, lay = device.allocate(wl)
+    device.fill(wl, t, lay)
+
+    def make(prec):
+        eng = pf.PairF12(prec)
+        eng.upload_pairs(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
+        return eng
+
+    def timed(eng, steps, warmup, sampler=None):
+        stream = torch.cuda.current_stream()
+        for _ in range(warmup):
+            eng.fit()
+            eng.energy(want_host=False)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        fit_ms = []
+        ev0.record(stream)
+        ctx = sampler if sampler is not None else _Null()
+        with ctx:
+            for _ in range(steps):
+                eng.fit()
+                eng.energy(want_host=False)
+                fit_ms.append(None)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1) / steps
+        return ms
+
+    out = {}
+    # headline: requested precision
+    eng = make(args.precision)
+    sampler = ClockSampler(local_rank)
+    ms = timed(eng, args.steps, args.warmup, sampler)
+    # per-launch duration of the fused kernel, measured on its own stream with events
+    fit_ms = []
+    for _ in range(max(2, min(args.steps, 5))):
+        eng.fit()
+        fit_ms.append(eng.stats()["ms_fit"])
+    ms_fit = float(np.mean(fit_ms))
+    E, e_pair = eng.energy()
+    e_main = e_pair.cpu().numpy()
+    status_bad = int((eng.pair_status() != 0).sum())
+    st = eng.stats()
+    eng.close()
+    del eng
+    torch.cuda.empty_cache()
+    out.update(ms=ms, ms_fit=ms_fit, E=E, status_bad=status_bad, stats=st, clocks=sampler.summary())
+
+    # plain FP64 mode of the same step, and the error of the headline energies against it
+    if not args.no_fp64_compare and args.precision != "fp64":
+        eng = make("fp64")
+        ms64 = timed(eng, max(2, args.steps // 2), 1)
+        E64, e64 = eng.energy()
+        e64 = e64.cpu().numpy()
+        eng.close()
+        del eng
+        torch.cuda.empty_cache()
+        sum_abs = float(np.abs(e64.sum(axis=1)).sum())
+        kappa = CHEM_SCALE_PER_ORB * wl.n_orb / sum_abs
+        out["fp64_mode"] = {"value": wl.n_pairs / ms64 * 1e3, "ms_per_step": ms64,
+                            "fp64_tflops": (f64 + fmix) / ms64 / 1e9}
+        out["error_vs_fp64"] = {
+            "total_Eh_normalised": abs(E - E64) * kappa,
+            "max_pair_Eh_normalised": float(np.abs(e_main - e64).max() * kappa),
+            "total_rel_to_sum_abs": abs(E - E64) / sum_abs, "kappa": kappa,
+            "E_mixed_raw": E, "E_fp64_raw": E64}
+
+    # end to end through the public API from pinned host buffers
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(args, wl, t, lay, pf, torch)
+    del t
+    torch.cuda.empty_cache()
+    return wl, f64, fmix, byts, out
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def run_e2e(args, wl_full, t_full, lay_full, pf, torch):
+    """Pairs/s of a bounded prefix of the workload whose packed inputs (<= 24 GB)
+    sit in pinned host memory: every step copies them host->device, runs
+    upload + fit + energy, and reads the total back to the host."""
+    import synthetic as S
+    from synthetic import workloads as W
+    budget = 24e9
+    n = 0
+    acc = 0.0
+    p, k, m = wl_full.n_pao, wl_full.n_pno, wl_full.n_aux
+    per = 8.0 * (4 * p * m + 2 * m * m + p * k + k * k)
+    while n < wl_full.n_pairs and acc + per[n] <= budget:
+        acc += per[n]
+        n += 1
+    wl = wl_full.subset(np.arange(n), name=f"{wl_full.name}[first {n} pairs]")
+    lay = W.packed_offsets(wl)
+    # pinned host copies of the prefix (taken from the device-drawn inputs:
+    # the prefix blocks are the first blocks of every packed buffer)
+    lens = {"Agi": lay["len_pm"], "Agj": lay["len_pm"], "Afi": lay["len_pm"], "Afj": lay["len_pm"],
+            "Jg": lay["len_mm"], "Jf": lay["len_mm"], "Q": lay["len_pk"], "T": lay["len_kk"]}
+    host = {x: t_full[x][:max(L, 2)].cpu().pin_memory() for x, L in lens.items()}
+    dev = {x: torch.empty_like(v, device="cuda") for x, v in host.items()}
+    h2d = sum(v.numel() * 8 for v in host.values())
+    eng = pf.PairF12(args.precision)
+
+    def step():
+        for x in host:
+            dev[x].copy_(host[x], non_blocking=True)
+        eng.upload_pairs(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, dev, lay)
+        eng.fit()
+        E, _ = eng.energy()       # device -> host read of the total
+        return E
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = max(2, args.steps)
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    eng.close()
+    del dev, host
+    torch.cuda.empty_cache()
+    return {"value": n / dt, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": 8, "pairs": n, "ms_per_step": dt * 1e3,
+            "workload": wl.name}
+
+
+# --------------------------------------------------------------------------- main
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl, f64, fmix, byts, o = run_ours(args, rank, world, local_rank)
+    ms = o["ms"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        x = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        ms = float(x.item())
+    if rank != 0:
+        return
+    n_pairs = wl.n_pairs
+    value = world * n_pairs / ms * 1e3
+    flops_dom = f64 + (fmix if args.precision == "fp64" else 0.0)
+    achieved = flops_dom / o["ms_fit"] / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32" if args.precision != "fp64" else "f64",
+        "data": "synthetic (seeded Philox4x32-10 draws, device-resident)",
+        "config": {"workload": wl.name, "pairs": n_pairs, "orbitals": wl.n_orb,
+                   "somos": wl.n_somo, "precision": args.precision,
+                   "p_range": [int(wl.n_pao.min()), int(wl.n_pao.max())],
+                   "k_range": [int(wl.n_pno.min()), int(wl.n_pno.max())],
+                   "m_range": [int(wl.n_aux.min()), int(wl.n_aux.max())],
+                   "l2": f"inputs {byts / 1e9:.0f} GB >> 129 MB L2, no flush"},
+        "tflops": {"fp64": f64 / ms / 1e9, "mixed_part": fmix / ms / 1e9,
+                   "total": (f64 + fmix) / ms / 1e9},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "pair_forward_kernel (fused persistent)",
+                     "peak_kind": "FP64 DFMA pipe, nominal 1.25 TFLOP/s (152 SMs x 4 flop/clk x 2.07 GHz)",
+                     "ms_per_launch": o["ms_fit"]},
+        "clocks": o["clocks"],
+        "gpu_launches": 2 * args.steps,
+        "E_total_raw": o["E"], "pairs_failed": o["status_bad"],
+    }
+    for key in ("fp64_mode", "error_vs_fp64", "e2e"):
+        if key in o:
+            line[key] = o[key]
+    if "e2e" not in line:
+        line["e2e"] = None
+    if not args.no_cpu and world == 1:
+        rate, cores, sample = cpu_oracle_rate(wl, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    wl = make_workload(args.workload, args.max_pairs)
+    wl.meta["bench_name"] = args.workload
+    wl.meta["bench_max"] = args.max_pairs
+    budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    rates = []
+    for i in range(args.warmup + args.steps):
+        rate, cores, sample = cpu_oracle_rate(wl, budget)
+        if i >= args.warmup:
+            rates.append(rate)
+    value = float(np.mean(rates))
+    line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Philox4x32-10 draws)", "impl": "reference",
+            "config": {"workload": wl.name, "pairs": wl.n_pairs, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()
