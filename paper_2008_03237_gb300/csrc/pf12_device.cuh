@@ -27,35 +27,47 @@ struct __align__(16) CholSmem {
 // for r0 <= r < min(r0 + 64, M), c0 <= c < min(c0 + 64, N), where
 //   A(r, t) = TA ? A[t * lda + r] : A[r * lda + t]
 //   B(t, c) = TB ? B[c * ldb + t] : B[t * ldb + c].
-// TC is the product type: double (FP64 FMAs) or float (FP32 FMAs over 32-wide
-// K chunks, each chunk's partial sum added to an FP64 accumulator).  Operands
-// may alias C's array as long as the tile's own C entries are not read as A/B.
-// Ends with all threads synchronised; C stores happen after the final barrier
-// and are read back only by the thread that wrote them.
+// Each of the 8 warps owns a 16 x 32 block of the tile (lane: 4 x 4 outputs,
+// rows lr + 4i, columns lc + 8j, conflict-free shared-memory reads).  A warp
+// whose block lies outside [0, M) x [0, N), or, when tri_rows > 0, entirely
+// above the diagonal within the first tri_rows rows, issues no arithmetic:
+// ragged edges and the upper halves of diagonal tiles cost no FP64 pipe time.
+// TC is the product type: double (FP64 FMAs) or float (FP32 FMAs; partial sums
+// over 128-wide K spans are added to FP64 accumulators).  Operands may alias
+// C's array as long as the tile's own C entries are not read as A/B.  All
+// threads must call; the C stores follow the last barrier and are read back
+// only by the thread that wrote them.
 template <typename TC, bool TA, bool TB>
 __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double* A, int64_t lda,
                                               const double* B, int64_t ldb, double* C,
                                               int64_t ldc, int r0, int c0, double alpha,
-                                              bool accumulate, GemmSmem& sm) {
+                                              bool accumulate, GemmSmem& sm, int tri_rows = 0) {
   TC (*as)[kTile + 1] = reinterpret_cast<TC (*)[kTile + 1]>(sm.buf);
   TC (*bs)[kTile + 1] = reinterpret_cast<TC (*)[kTile + 1]>(sm.buf + kBK * (kTile + 1));
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wr = 16 * (warp >> 1), wc = 32 * (warp & 1);   // warp block offsets in the tile
+  const int lr = lane >> 3, lc = lane & 7;
+  const int br = r0 + wr, bc = c0 + wc;                      // warp block origin (global)
+  bool active = br < M && bc < N;
+  if (tri_rows > 0 && br + 15 < tri_rows && bc > br + 15) active = false;
   double accd[4][4];
+  float accf[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) accd[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) { accd[i][j] = 0.0; accf[i][j] = 0.0f; }
 
-  for (int k0 = 0; k0 < K; k0 += kBK) {
+  int chunk = 0;
+  for (int k0 = 0; k0 < K; k0 += kBK, ++chunk) {
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       int r, t;
       if (!TA) { t = tid & 31; r = (tid >> 5) + 8 * s; }
       else     { r = tid & 63; t = (tid >> 6) + 4 * s; }
       const int gr = r0 + r, gt = k0 + t;
-      double v = 0.0;
-      if (gr < M && gt < K) v = TA ? A[(int64_t)gt * lda + gr] : A[(int64_t)gr * lda + gt];
-      as[t][r] = (TC)v;
+      TC v = TC(0);
+      if (gr < M && gt < K) v = (TC)(TA ? A[(int64_t)gt * lda + gr] : A[(int64_t)gr * lda + gt]);
+      as[t][r] = v;
     }
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
@@ -63,70 +75,71 @@ __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double*
       if (TB) { t = tid & 31; c = (tid >> 5) + 8 * s; }
       else    { c = tid & 63; t = (tid >> 6) + 4 * s; }
       const int gc = c0 + c, gt = k0 + t;
-      double v = 0.0;
-      if (gc < N && gt < K) v = TB ? B[(int64_t)gc * ldb + gt] : B[(int64_t)gt * ldb + gc];
-      bs[t][c] = (TC)v;
+      TC v = TC(0);
+      if (gc < N && gt < K) v = (TC)(TB ? B[(int64_t)gc * ldb + gt] : B[(int64_t)gt * ldb + gc]);
+      bs[t][c] = v;
     }
     __syncthreads();
-    const int kn = min(kBK, K - k0);
-    if constexpr (sizeof(TC) == sizeof(double)) {
-      if (kn == kBK) {
+    if (active) {
+      const int kn = min(kBK, K - k0);
+      if constexpr (sizeof(TC) == sizeof(double)) {
+        if (kn == kBK) {
 #pragma unroll 8
-        for (int kk = 0; kk < kBK; ++kk) {
-          double a[4], b[4];
+          for (int kk = 0; kk < kBK; ++kk) {
+            double a[4], b[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = as[kk][ty + 16 * i];
+            for (int i = 0; i < 4; ++i) a[i] = as[kk][wr + lr + 4 * i];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) b[j] = bs[kk][tx + 16 * j];
+            for (int j = 0; j < 4; ++j) b[j] = bs[kk][wc + lc + 8 * j];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) accd[i][j] = fma(a[i], b[j], accd[i][j]);
+              for (int j = 0; j < 4; ++j) accd[i][j] = fma(a[i], b[j], accd[i][j]);
+          }
+        } else {
+          for (int kk = 0; kk < kn; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = as[kk][wr + lr + 4 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = bs[kk][wc + lc + 8 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) accd[i][j] = fma(a[i], b[j], accd[i][j]);
+          }
         }
       } else {
+#pragma unroll 4
         for (int kk = 0; kk < kn; ++kk) {
-          double a[4], b[4];
+          float a[4], b[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = as[kk][ty + 16 * i];
+          for (int i = 0; i < 4; ++i) a[i] = as[kk][wr + lr + 4 * i];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) b[j] = bs[kk][tx + 16 * j];
+          for (int j = 0; j < 4; ++j) b[j] = bs[kk][wc + lc + 8 * j];
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) accd[i][j] = fma(a[i], b[j], accd[i][j]);
+            for (int j = 0; j < 4; ++j) accf[i][j] = fmaf(a[i], b[j], accf[i][j]);
+        }
+        if ((chunk & 3) == 3 || k0 + kBK >= K) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { accd[i][j] += (double)accf[i][j]; accf[i][j] = 0.0f; }
         }
       }
-    } else {
-      float acc[4][4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-      for (int kk = 0; kk < kn; ++kk) {
-        float a[4], b[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = as[kk][ty + 16 * i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = bs[kk][tx + 16 * j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) accd[i][j] += (double)acc[i][j];
     }
     __syncthreads();
   }
+  if (!active) return;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int r = r0 + ty + 16 * i;
+    const int r = br + lr + 4 * i;
     if (r >= M) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int c = c0 + tx + 16 * j;
+      const int c = bc + lc + 8 * j;
       if (c >= N) continue;
       double* pc = C + (int64_t)r * ldc + c;
       *pc = accumulate ? fma(alpha, accd[i][j], *pc) : alpha * accd[i][j];
@@ -213,7 +226,7 @@ __device__ __forceinline__ bool chol_augmented(double* M, int64_t ld, int m, int
     for (int R = rb; R < rows; R += kTile)
       for (int C = rb; C < m && C < R + kTile; C += kTile)
         cta_gemm_tile<double, false, true>(rows, m, nb, M + kb, ld, M + kb, ld, M, ld, R, C, -1.0,
-                                           true, gs);
+                                           true, gs, m);
     __syncthreads();
   }
   return true;
