@@ -184,6 +184,34 @@ const char* pf12_last_error(const pf12_ctx* ctx);
 /* Release the context's workspace, graph and metadata. */
 void pf12_destroy(pf12_ctx* ctx);
 
+/* Allocation-free forward pass: steps 1-6 for every pair in one call, with
+ * no cudaMalloc, cudaFree or other allocating call.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate
+ * device memory themselves or through the library (code running inside a
+ * memory pool or arena it does not own, plugins whose host program owns
+ * every device allocation, callers just refused more memory).
+ *   Scratch: a fixed 64 MiB file-scope device array inside the library,
+ *     held by every GPU that loads it until the process exits.  One call
+ *     needs 84 B per pair of metadata (+ 1 KiB) plus one Cholesky/solve slab of
+ *     8 ((m + 2k) ld + 2k ld + 64) bytes (ld = m rounded up to 4) for the
+ *     largest pair; sizes beyond that return PF12_ERR_INVALID_ARG.  The
+ *     number of concurrent pairs is whatever number of slabs fits (at most
+ *     2 per SM), pairs are taken in the caller's order.
+ *   Set-up: the first call on each device looks up the array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that
+ *     first call before any stream capture.
+ *   Sharing: every call uses the same array and leaves the last call's
+ *     contents in it; calls whose GPU work overlaps (other streams or host
+ *     threads) race on it and must be serialised by the caller.
+ *   Arguments as pf12_upload_pairs plus: precision (pf12_precision), stream
+ *   (cudaStream_t, NULL = legacy stream), V_dev (device, len_kk doubles, out:
+ *   V in the T layout), e_pair_dev (device, n_pairs x 3, out), E_host (host,
+ *   out, may be NULL).  Synchronises the stream.  Returns as pf12_energy. */
+int pf12_energy_noalloc(int32_t n_orb, const int8_t* orb_kind, int64_t n_pairs, const int32_t* pi,
+                        const int32_t* pj, const int32_t* n_pao, const int32_t* n_pno,
+                        const int32_t* n_aux, const pf12_tensors* t, int32_t precision,
+                        void* cuda_stream, double* V_dev, double* e_pair_dev, double* E_host);
+
 #ifdef __cplusplus
 }
 #endif

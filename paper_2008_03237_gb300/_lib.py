@@ -52,6 +52,10 @@ SIGNATURES = {
     "pf12_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "pf12_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "pf12_destroy": (None, [ctypes.c_void_p]),
+    "pf12_energy_noalloc": (ctypes.c_int, [ctypes.c_int32, c_i8p, ctypes.c_int64, c_i32p, c_i32p,
+                                           c_i32p, c_i32p, c_i32p, ctypes.POINTER(Tensors),
+                                           ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, c_dp]),
 }
 
 _lib = None
