@@ -382,6 +382,9 @@ def main():
         "clocks": o["clocks"],
         "gpu_launches": 2 * args.steps,
         "E_total_raw": o["E"], "pairs_failed": o["status_bad"],
+        "autotuner": {"variant": o["stats"]["tile_config"],
+                      "variants": ["2 CTAs/SM", "3 CTAs/SM"],
+                      "sample_ms": o["stats"]["tune_ms"]},
     }
     for key in ("fp64_mode", "error_vs_fp64", "e2e"):
         if key in o:

@@ -118,8 +118,9 @@ typedef struct {
   int64_t n_pairs;
   int32_t n_ctas;        /* persistent CTAs of the fused pair kernel */
   int32_t launches_fit;  /* kernels launched by one pf12_fit */
-  int32_t tile_config;   /* autotuner choice (index) */
+  int32_t tile_config;   /* autotuner choice: forward variant (0: 2 CTAs/SM, 1: 3 CTAs/SM) */
   int32_t graph_used;    /* 1 when pf12_fit replays a captured CUDA graph */
+  double tune_ms[2];     /* autotuner timings of the variants on its sample (0 if not tuned) */
 } pf12_stats_t;
 
 /* Create a context.  opts may be NULL (FP64, legacy stream, no cap). */

@@ -55,9 +55,10 @@ class PairF12:
     precision: "fp64" (plain mode) or "mixed_fp32".  FP64 Cholesky, solves and
     energy sums in both."""
 
-    def __init__(self, precision="fp64", workspace_bytes=0, stream=None):
+    def __init__(self, precision="fp64", workspace_bytes=0, stream=None, tuner_cache=None):
         self._L = lib()
-        opts = _lib.Opts(_lib.PRECISION[precision], None, int(workspace_bytes), 1, None)
+        self._cache = tuner_cache.encode() if tuner_cache else None
+        opts = _lib.Opts(_lib.PRECISION[precision], None, int(workspace_bytes), 1, self._cache)
         h = ctypes.c_void_p()
         self._check(self._L.pf12_create(ctypes.byref(h), ctypes.byref(opts)), None)
         self._h = h
@@ -152,7 +153,9 @@ class PairF12:
     def stats(self):
         s = _lib.Stats()
         self._check(self._L.pf12_stats(self._h, ctypes.byref(s)))
-        return {n: getattr(s, n) for n, _ in _lib.Stats._fields_}
+        out = {n: getattr(s, n) for n, _ in _lib.Stats._fields_}
+        out["tune_ms"] = list(s.tune_ms)
+        return out
 
 
 class PairF12Energy(torch.autograd.Function):

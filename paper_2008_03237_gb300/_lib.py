@@ -34,7 +34,7 @@ class Stats(ctypes.Structure):
                 ("flops_mixed", ctypes.c_double), ("bytes_in", ctypes.c_double),
                 ("n_pairs", ctypes.c_int64), ("n_ctas", ctypes.c_int32),
                 ("launches_fit", ctypes.c_int32), ("tile_config", ctypes.c_int32),
-                ("graph_used", ctypes.c_int32)]
+                ("graph_used", ctypes.c_int32), ("tune_ms", ctypes.c_double * 2)]
 
 
 # name -> (restype, argtypes); the same names as the C entry points

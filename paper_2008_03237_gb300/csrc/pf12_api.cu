@@ -43,6 +43,15 @@ struct pf12_ctx {
   int n_ctas = 0, n_ctas_bwd = 0;
   int64_t max_fwd_ws = 0, max_bwd_ws = 0;
 
+  // autotuner: forward kernel variant (occupancy), its CTA counts, tuning sample
+  int variant = -1;
+  int n_ctas_v[pf12::kFwdVariants] = {};
+  std::string tuner_cache;
+  std::string tune_key;
+  double tune_ms[pf12::kFwdVariants] = {};
+  PairDesc* d_desc_sample = nullptr;
+  int64_t n_sample = 0;
+
   // graph of the forward launch
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -72,6 +81,10 @@ int cuda_fail(pf12_ctx* c, cudaError_t e, const char* where) {
 
 void free_pairs(pf12_ctx* c) {
   cudaFree(c->d_desc);
+  cudaFree(c->d_desc_sample);
+  c->d_desc_sample = nullptr;
+  c->n_sample = 0;
+  c->variant = -1;
   cudaFree(c->d_V);
   cudaFree(c->d_epair);
   cudaFree(c->d_dx);
@@ -131,6 +144,7 @@ int pf12_create(pf12_ctx** out, const pf12_opts* o) {
     c->precision = o->precision;
     c->stream = static_cast<cudaStream_t>(o->cuda_stream);
     c->ws_cap = o->workspace_bytes;
+    if (o->tuner_cache) c->tuner_cache = o->tuner_cache;
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -243,28 +257,55 @@ int pf12_upload_pairs(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_
   c->max_fwd_ws = max_fwd;
   c->max_bwd_ws = max_bwd;
 
-  // workspace: one slab per persistent CTA, shared by forward and backward
-  const int bps = std::max(1, pf12::forward_blocks_per_sm(c->precision));
-  const int bps_b = std::max(1, pf12::backward_blocks_per_sm(c->precision));
-  int64_t want = std::min<int64_t>(n_pairs, (int64_t)bps * c->n_sm);
-  int64_t want_b = std::min<int64_t>(n_pairs, (int64_t)bps_b * c->n_sm);
-  want = std::max<int64_t>(want, 1);
-  want_b = std::max<int64_t>(want_b, 1);
+  // workspace: one slab per persistent CTA, shared by forward and backward;
+  // sized for the forward variant with the most resident CTAs
   const int64_t stride = (max_fwd + 31) / 32 * 32;
   const int64_t stride_b = (max_bwd + 31) / 32 * 32;
+  int64_t cap_f = INT64_MAX, cap_b = INT64_MAX;
   if (c->ws_cap) {
-    const int64_t fit_f = (int64_t)(c->ws_cap / 8) / std::max<int64_t>(stride, 1);
-    const int64_t fit_b = (int64_t)(c->ws_cap / 8) / std::max<int64_t>(stride_b, 1);
-    if (n_pairs > 0 && (fit_f < 1 || fit_b < 1))
+    cap_f = (int64_t)(c->ws_cap / 8) / std::max<int64_t>(stride, 1);
+    cap_b = (int64_t)(c->ws_cap / 8) / std::max<int64_t>(stride_b, 1);
+    if (n_pairs > 0 && (cap_f < 1 || cap_b < 1))
       return fail(c, PF12_ERR_OOM, "workspace_bytes too small for the largest pair");
-    want = std::min(want, fit_f);
-    want_b = std::min(want_b, fit_b);
   }
-  c->n_ctas = (int)want;
+  int64_t want = 1;
+  for (int v = 0; v < pf12::kFwdVariants; ++v) {
+    const int bps = std::max(1, pf12::forward_blocks_per_sm(c->precision, v));
+    int64_t n_v = std::min<int64_t>(n_pairs, (int64_t)bps * c->n_sm);
+    n_v = std::max<int64_t>(1, std::min(n_v, cap_f));
+    c->n_ctas_v[v] = (int)n_v;
+    want = std::max(want, n_v);
+  }
+  const int bps_b = std::max(1, pf12::backward_blocks_per_sm(c->precision));
+  int64_t want_b = std::min<int64_t>(n_pairs, (int64_t)bps_b * c->n_sm);
+  want_b = std::max<int64_t>(1, std::min(want_b, cap_b));
+  c->n_ctas = c->n_ctas_v[0];
   c->n_ctas_bwd = (int)want_b;
   c->ws_stride = stride;
   c->ws_stride_bwd = stride_b;
   const size_t work_doubles = (size_t)std::max(want * stride, want_b * stride_b);
+
+  // tuning sample: pairs spread evenly over the cost-sorted list
+  std::vector<PairDesc> sample;
+  const int64_t n_s = std::min<int64_t>(n_pairs, 3 * (int64_t)want);
+  for (int64_t q = 0; q < n_s; ++q) sample.push_back(sorted[(q * n_pairs) / std::max<int64_t>(n_s, 1)]);
+  {
+    std::vector<int> ms, ks;
+    for (int64_t P = 0; P < n_pairs; ++P) { ms.push_back(n_aux[P]); ks.push_back(n_pno[P]); }
+    std::sort(ms.begin(), ms.end());
+    std::sort(ks.begin(), ks.end());
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    char key[256];
+    snprintf(key, sizeof key, "%s|sm%d|prec%d|m%d|k%d|n%d", prop.name, c->n_sm, c->precision,
+             n_pairs ? ms[n_pairs / 2] / 50 * 50 : 0, n_pairs ? ks[n_pairs / 2] / 5 * 5 : 0,
+             n_pairs ? (int)std::log2((double)n_pairs) : 0);
+    c->tune_key = key;
+    for (char& ch : c->tune_key)
+      if (ch == ' ') ch = '_';
+  }
 
   const size_t n = (size_t)std::max<int64_t>(n_pairs, 1);
   cudaError_t e = cudaSuccess;
@@ -276,6 +317,7 @@ int pf12_upload_pairs(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_
   if (e == cudaSuccess) e = cudaMalloc(&c->d_out3, sizeof(double) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, sizeof(int32_t) * 2);
   if (e == cudaSuccess && n_pairs > 0) e = cudaMalloc(&c->d_work, sizeof(double) * work_doubles);
+  if (e == cudaSuccess && n_s > 0) e = cudaMalloc(&c->d_desc_sample, sizeof(PairDesc) * n_s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_pairs(c);
@@ -285,6 +327,10 @@ int pf12_upload_pairs(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_
   c->work_bytes = sizeof(double) * work_doubles;
   PF12_CUDA(c, cudaMemcpyAsync(c->d_desc, sorted.data(), sizeof(PairDesc) * n_pairs,
                                cudaMemcpyHostToDevice, c->stream));
+  if (n_s > 0)
+    PF12_CUDA(c, cudaMemcpyAsync(c->d_desc_sample, sample.data(), sizeof(PairDesc) * n_s,
+                                 cudaMemcpyHostToDevice, c->stream));
+  c->n_sample = n_s;
   if (t && t->len_kk > 0) PF12_CUDA(c, cudaMemsetAsync(c->d_V, 0, sizeof(double) * t->len_kk, c->stream));
   PF12_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int32_t) * n, c->stream));
   PF12_CUDA(c, cudaMemsetAsync(c->d_epair, 0, sizeof(double) * 3 * n, c->stream));
@@ -293,6 +339,64 @@ int pf12_upload_pairs(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_
   return PF12_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Autotuner: time every forward variant on the cost-spread sample of this pair
+// list (one warm-up launch on a single pair, then one timed launch) and keep the
+// fastest.  Results are cached per (GPU, precision, size signature) in the
+// optional tuner_cache file, one "key variant ms0 ms1" line per entry.
+int tune(pf12_ctx* c) {
+  if (!c->tuner_cache.empty()) {
+    FILE* f = fopen(c->tuner_cache.c_str(), "r");
+    if (f) {
+      char key[512];
+      int v = -1;
+      while (fscanf(f, "%511s %d %*f %*f", key, &v) == 2)
+        if (c->tune_key == key && v >= 0 && v < pf12::kFwdVariants) c->variant = v;
+      fclose(f);
+    }
+    if (c->variant >= 0) return PF12_OK;
+  }
+  // small lists: one wave of CTAs at most, nothing to tune
+  if (c->n_pairs <= c->n_ctas_v[0] || c->n_sample == 0) {
+    c->variant = 0;
+    return PF12_OK;
+  }
+  pf12::FwdParams f = fwd_params(c);
+  f.desc = c->d_desc_sample;
+  int best = 0;
+  for (int v = 0; v < pf12::kFwdVariants; ++v) {
+    f.n_pairs = 1;
+    PF12_CUDA(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->stream));
+    PF12_CUDA(c, pf12::launch_forward(f, c->precision, v, 1, c->stream));
+    f.n_pairs = c->n_sample;
+    PF12_CUDA(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->stream));
+    PF12_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+    PF12_CUDA(c, pf12::launch_forward(f, c->precision, v, c->n_ctas_v[v], c->stream));
+    PF12_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+    PF12_CUDA(c, cudaEventSynchronize(c->ev[1]));
+    float ms = 0;
+    PF12_CUDA(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+    c->tune_ms[v] = ms;
+    if (ms < c->tune_ms[best]) best = v;
+  }
+  c->variant = best;
+  if (!c->tuner_cache.empty()) {
+    FILE* fo = fopen(c->tuner_cache.c_str(), "a");
+    if (fo) {
+      fprintf(fo, "%s %d %.3f %.3f\n", c->tune_key.c_str(), best, c->tune_ms[0], c->tune_ms[1]);
+      fclose(fo);
+    }
+  }
+  return PF12_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int pf12_fit(pf12_ctx* c) {
   if (!c) return PF12_ERR_INVALID_ARG;
   if (!c->uploaded) return fail(c, PF12_ERR_INVALID_ARG, "pf12_fit before pf12_upload_pairs");
@@ -300,11 +404,17 @@ int pf12_fit(pf12_ctx* c) {
     c->fitted = true;
     return PF12_OK;
   }
+  if (c->variant < 0) {
+    const int rc = tune(c);
+    if (rc != PF12_OK) return rc;
+    c->n_ctas = c->n_ctas_v[c->variant];
+  }
   if (!c->graph_exec) {
     // capture on the library's own stream (nothing executes), replay on the caller's
     PF12_CUDA(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->capture_stream);
-    if (e == cudaSuccess) e = pf12::launch_forward(fwd_params(c), c->precision, c->n_ctas, c->capture_stream);
+    if (e == cudaSuccess)
+      e = pf12::launch_forward(fwd_params(c), c->precision, c->variant, c->n_ctas, c->capture_stream);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &g);
     if (e != cudaSuccess) return cuda_fail(c, e, "capture forward");
@@ -415,7 +525,9 @@ int pf12_stats(pf12_ctx* c, pf12_stats_t* s) {
   s->n_pairs = c->n_pairs;
   s->n_ctas = c->n_ctas;
   s->launches_fit = c->n_pairs > 0 ? 1 : 0;
-  s->tile_config = 0;
+  s->tile_config = c->variant;
+  s->tune_ms[0] = c->tune_ms[0];
+  s->tune_ms[1] = c->tune_ms[1];
   s->graph_used = c->graph_exec != nullptr;
   return PF12_OK;
 }

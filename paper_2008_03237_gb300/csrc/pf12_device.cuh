@@ -27,11 +27,13 @@ struct __align__(16) CholSmem {
 // for r0 <= r < min(r0 + 64, M), c0 <= c < min(c0 + 64, N), where
 //   A(r, t) = TA ? A[t * lda + r] : A[r * lda + t]
 //   B(t, c) = TB ? B[c * ldb + t] : B[t * ldb + c].
-// Each of the 8 warps owns a 16 x 32 block of the tile (lane: 4 x 4 outputs,
-// rows lr + 4i, columns lc + 8j, conflict-free shared-memory reads).  A warp
-// whose block lies outside [0, M) x [0, N), or, when tri_rows > 0, entirely
-// above the diagonal within the first tri_rows rows, issues no arithmetic:
-// ragged edges and the upper halves of diagonal tiles cost no FP64 pipe time.
+// The 64 x 64 tile is split into 32 blocks of 8 x 16.  A block is active when
+// it meets [0, M) x [0, N) and, if tri_rows > 0, is not entirely above the
+// diagonal within the first tri_rows rows.  Active blocks are dealt
+// round-robin to the 8 warps (at most 4 each; lane: 2 x 2 outputs, rows
+// lr + 4i, columns lc + 8j, conflict-free shared-memory reads), so ragged
+// edges and the upper halves of diagonal tiles cost no arithmetic and the
+// remaining work is spread evenly over the warps.
 // TC is the product type: double (FP64 FMAs) or float (FP32 FMAs; partial sums
 // over 128-wide K spans are added to FP64 accumulators).  Operands may alias
 // C's array as long as the tile's own C entries are not read as A/B.  All
@@ -45,17 +47,35 @@ __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double*
   TC (*as)[kTile + 1] = reinterpret_cast<TC (*)[kTile + 1]>(sm.buf);
   TC (*bs)[kTile + 1] = reinterpret_cast<TC (*)[kTile + 1]>(sm.buf + kBK * (kTile + 1));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wr = 16 * (warp >> 1), wc = 32 * (warp & 1);   // warp block offsets in the tile
   const int lr = lane >> 3, lc = lane & 7;
-  const int br = r0 + wr, bc = c0 + wc;                      // warp block origin (global)
-  bool active = br < M && bc < N;
-  if (tri_rows > 0 && br + 15 < tri_rows && bc > br + 15) active = false;
-  double accd[4][4];
-  float accf[4][4];
+  // this warp's blocks: tile-local origins (row, col); -1 = unused slot
+  int orow[4] = {-1, -1, -1, -1}, ocol[4] = {0, 0, 0, 0};
+  {
+    int cnt = 0, slot = 0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int b = 0; b < 32; ++b) {
+      const int br = r0 + 8 * (b >> 2), bc = c0 + 16 * (b & 3);
+      bool act = br < M && bc < N;
+      if (tri_rows > 0 && br + 7 < tri_rows && bc > br + 7) act = false;
+      if (act) {
+        if ((cnt & 7) == warp && slot < 4) {
+          orow[slot] = 8 * (b >> 2);
+          ocol[slot] = 16 * (b & 3);
+          ++slot;
+        }
+        ++cnt;
+      }
+    }
+  }
+  const bool any = orow[0] >= 0;
+  double accd[4][2][2];
+  float accf[4][2][2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { accd[i][j] = 0.0; accf[i][j] = 0.0f; }
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) { accd[q][i][j] = 0.0; accf[q][i][j] = 0.0f; }
 
   int chunk = 0;
   for (int k0 = 0; k0 < K; k0 += kBK, ++chunk) {
@@ -80,69 +100,65 @@ __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double*
       bs[t][c] = v;
     }
     __syncthreads();
-    if (active) {
+    if (any) {
       const int kn = min(kBK, K - k0);
       if constexpr (sizeof(TC) == sizeof(double)) {
-        if (kn == kBK) {
-#pragma unroll 8
-          for (int kk = 0; kk < kBK; ++kk) {
-            double a[4], b[4];
+#pragma unroll 4
+        for (int kk = 0; kk < kn; ++kk) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = as[kk][wr + lr + 4 * i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = bs[kk][wc + lc + 8 * j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int j = 0; j < 4; ++j) accd[i][j] = fma(a[i], b[j], accd[i][j]);
-          }
-        } else {
-          for (int kk = 0; kk < kn; ++kk) {
-            double a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = as[kk][wr + lr + 4 * i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = bs[kk][wc + lc + 8 * j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int j = 0; j < 4; ++j) accd[i][j] = fma(a[i], b[j], accd[i][j]);
+          for (int q = 0; q < 4; ++q) {
+            if (orow[q] < 0) continue;
+            const double a0 = as[kk][orow[q] + lr], a1 = as[kk][orow[q] + lr + 4];
+            const double b0 = bs[kk][ocol[q] + lc], b1 = bs[kk][ocol[q] + lc + 8];
+            accd[q][0][0] = fma(a0, b0, accd[q][0][0]);
+            accd[q][0][1] = fma(a0, b1, accd[q][0][1]);
+            accd[q][1][0] = fma(a1, b0, accd[q][1][0]);
+            accd[q][1][1] = fma(a1, b1, accd[q][1][1]);
           }
         }
       } else {
 #pragma unroll 4
         for (int kk = 0; kk < kn; ++kk) {
-          float a[4], b[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = as[kk][wr + lr + 4 * i];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) b[j] = bs[kk][wc + lc + 8 * j];
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) accf[i][j] = fmaf(a[i], b[j], accf[i][j]);
+          for (int q = 0; q < 4; ++q) {
+            if (orow[q] < 0) continue;
+            const float a0 = as[kk][orow[q] + lr], a1 = as[kk][orow[q] + lr + 4];
+            const float b0 = bs[kk][ocol[q] + lc], b1 = bs[kk][ocol[q] + lc + 8];
+            accf[q][0][0] = fmaf(a0, b0, accf[q][0][0]);
+            accf[q][0][1] = fmaf(a0, b1, accf[q][0][1]);
+            accf[q][1][0] = fmaf(a1, b0, accf[q][1][0]);
+            accf[q][1][1] = fmaf(a1, b1, accf[q][1][1]);
+          }
         }
         if ((chunk & 3) == 3 || k0 + kBK >= K) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) { accd[i][j] += (double)accf[i][j]; accf[i][j] = 0.0f; }
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+              for (int j = 0; j < 2; ++j) {
+                if (orow[q] >= 0) accd[q][i][j] += (double)accf[q][i][j];
+                accf[q][i][j] = 0.0f;
+              }
         }
       }
     }
     __syncthreads();
   }
-  if (!active) return;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = br + lr + 4 * i;
-    if (r >= M) continue;
+  for (int q = 0; q < 4; ++q) {
+    if (orow[q] < 0) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = bc + lc + 8 * j;
-      if (c >= N) continue;
-      double* pc = C + (int64_t)r * ldc + c;
-      *pc = accumulate ? fma(alpha, accd[i][j], *pc) : alpha * accd[i][j];
+    for (int i = 0; i < 2; ++i) {
+      const int r = r0 + orow[q] + lr + 4 * i;
+      if (r >= M) continue;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int c = c0 + ocol[q] + lc + 8 * j;
+        if (c >= N) continue;
+        double* pc = C + (int64_t)r * ldc + c;
+        *pc = accumulate ? fma(alpha, accd[q][i][j], *pc) : alpha * accd[q][i][j];
+      }
     }
   }
 }

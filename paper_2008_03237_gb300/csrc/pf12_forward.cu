@@ -100,8 +100,8 @@ __device__ void pair_forward(const FwdParams& prm, const PairDesc& pd, double* w
   }
 }
 
-template <typename TC>
-__global__ void __launch_bounds__(kThreads, 2) pair_forward_kernel(FwdParams prm) {
+template <typename TC, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) pair_forward_kernel(FwdParams prm) {
   __shared__ GemmSmem gs;
   __shared__ CholSmem cs;
   __shared__ double red[2][kThreads / 32];
@@ -119,20 +119,34 @@ __global__ void __launch_bounds__(kThreads, 2) pair_forward_kernel(FwdParams prm
   }
 }
 
-cudaError_t launch_forward(const FwdParams& prm, int precision, int n_ctas, cudaStream_t s) {
-  if (precision == 0)
-    pair_forward_kernel<double><<<n_ctas, kThreads, 0, s>>>(prm);
-  else
-    pair_forward_kernel<float><<<n_ctas, kThreads, 0, s>>>(prm);
+// Tile/occupancy variants the autotuner chooses from: variant v runs MINB = 2 + v
+// CTAs per SM (more resident pairs per SM hide the serial phases of each
+// pair's factorisation; fewer leave more registers per thread).
+cudaError_t launch_forward(const FwdParams& prm, int precision, int variant, int n_ctas,
+                           cudaStream_t s) {
+  if (precision == 0) {
+    if (variant == 1) pair_forward_kernel<double, 3><<<n_ctas, kThreads, 0, s>>>(prm);
+    else pair_forward_kernel<double, 2><<<n_ctas, kThreads, 0, s>>>(prm);
+  } else {
+    if (variant == 1) pair_forward_kernel<float, 3><<<n_ctas, kThreads, 0, s>>>(prm);
+    else pair_forward_kernel<float, 2><<<n_ctas, kThreads, 0, s>>>(prm);
+  }
   return cudaGetLastError();
 }
 
-int forward_blocks_per_sm(int precision) {
+int forward_blocks_per_sm(int precision, int variant) {
   int n = 0;
-  if (precision == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_kernel<double>, kThreads, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_kernel<float>, kThreads, 0);
+  if (precision == 0) {
+    if (variant == 1)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_kernel<double, 3>, kThreads, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_kernel<double, 2>, kThreads, 0);
+  } else {
+    if (variant == 1)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_kernel<float, 3>, kThreads, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_kernel<float, 2>, kThreads, 0);
+  }
   return n;
 }
 
@@ -305,7 +319,7 @@ extern "C" int pf12_energy_noalloc(int32_t n_orb, const int8_t* kind, int64_t n_
   // the queue head must start at zero; status, dx and slabs are fully written
   if (cudaMemsetAsync(base, 0, 256, s) != cudaSuccess) return PF12_ERR_CUDA;
 
-  const int bps = std::max(1, forward_blocks_per_sm(precision));
+  const int bps = std::max(1, forward_blocks_per_sm(precision, 0));
   int64_t n_ctas = std::min<int64_t>(n_pairs, (int64_t)bps * n_sm);
   n_ctas = std::min<int64_t>(n_ctas, (int64_t)((kNoallocScratchBytes - off_work) / stride));
   FwdParams f{};
@@ -326,7 +340,7 @@ extern "C" int pf12_energy_noalloc(int32_t n_orb, const int8_t* kind, int64_t n_
   f.work = reinterpret_cast<double*>(base + off_work);
   f.ws_stride = (int64_t)(stride / sizeof(double));
   f.counter = reinterpret_cast<int32_t*>(base);
-  if (launch_forward(f, precision, (int)n_ctas, s) != cudaSuccess) return PF12_ERR_CUDA;
+  if (launch_forward(f, precision, 0, (int)n_ctas, s) != cudaSuccess) return PF12_ERR_CUDA;
   double* out3 = reinterpret_cast<double*>(base + off_out3);
   if (launch_energy_total(e_pair_dev, f.status, n_pairs, out3, s) != cudaSuccess) return PF12_ERR_CUDA;
   double h3[3] = {0, 0, 0};

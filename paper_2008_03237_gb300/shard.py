@@ -1,0 +1,58 @@
+"""Pair-list sharding across ranks (host logic of the multi-GPU path).
+
+Pairs are independent, so ranks share no data: each rank evaluates its shard
+and the totals meet once at the end.  Shards are built by longest-processing-
+time assignment on the FP64 cost model m^3/3 + 4 k m^2 plus the mixable part;
+the final energy is summed in pair-list order on every rank, so the result is
+bitwise identical to a single-rank run whatever the number of ranks.
+"""
+import heapq
+
+import numpy as np
+
+
+def pair_costs(n_pao, n_pno, n_aux):
+    p, k, m = (np.asarray(a, np.float64) for a in (n_pao, n_pno, n_aux))
+    return m ** 3 / 3.0 + 4.0 * k * m * m + (8.0 * p * k * m + 2.0 * k * m * m + 4.0 * k * k * m) / 8.0
+
+
+def lpt_partition(costs, n_ranks):
+    """Deterministic LPT: pairs by decreasing cost (ties: list order) go to the
+    least-loaded rank (ties: lowest rank).  Returns one sorted index array per rank."""
+    order = np.argsort(-np.asarray(costs, np.float64), kind="stable")
+    heap = [(0.0, r) for r in range(n_ranks)]
+    out = [[] for _ in range(n_ranks)]
+    for P in order:
+        load, r = heapq.heappop(heap)
+        out[r].append(int(P))
+        heapq.heappush(heap, (load + float(costs[P]), r))
+    return [np.array(sorted(s), np.int64) for s in out]
+
+
+def gather_pair_energies(e_local, shard, n_pairs, group=None):
+    """All-gather every rank's (n_local x 3) pair energies into the full
+    (n_pairs x 3) array in pair-list order, then the FP64 total summed in that
+    order.  Uses torch.distributed (gloo on CPU, NCCL on GPUs)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    e_local = torch.as_tensor(np.asarray(e_local, np.float64)).reshape(-1, 3)
+    idx_local = torch.as_tensor(np.asarray(shard, np.int64))
+    sizes = [None] * world
+    dist.all_gather_object(sizes, int(idx_local.numel()), group=group)
+    nmax = max(sizes)
+    pad_e = torch.zeros((nmax, 3), dtype=torch.float64)
+    pad_i = torch.full((nmax,), -1, dtype=torch.int64)
+    pad_e[:e_local.shape[0]] = e_local
+    pad_i[:idx_local.numel()] = idx_local
+    all_e = [torch.zeros_like(pad_e) for _ in range(world)]
+    all_i = [torch.zeros_like(pad_i) for _ in range(world)]
+    dist.all_gather(all_e, pad_e, group=group)
+    dist.all_gather(all_i, pad_i, group=group)
+    full = np.full((n_pairs, 3), np.nan)
+    for e, i, n in zip(all_e, all_i, sizes):
+        full[i[:n].numpy()] = e[:n].numpy()
+    total = 0.0
+    for P in range(n_pairs):
+        total += full[P, 0] + full[P, 1] + full[P, 2]
+    return full, total
