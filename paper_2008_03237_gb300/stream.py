@@ -1,0 +1,103 @@
+"""Pair-streamed execution for pair lists whose inputs exceed device memory.
+
+The pair list is cut into contiguous batches whose packed inputs fit a byte
+budget.  For each batch a caller-supplied producer fills reused device buffers
+(integral code in an application, the synthetic generator in the tests and the
+benchmark); the library then runs the fused forward launch, the pair energies
+and optionally the adjoint on that batch.  Pair energies land in one device
+array in pair-list order; the total is the FP64 sum of the batch totals in
+batch order, so it is deterministic for a given budget.
+"""
+import numpy as np
+import torch
+
+from . import PairF12
+
+ALIGN = 32  # packed blocks start on multiples of 32 doubles (256 B)
+
+
+def packed_layout(n_pao, n_pno, n_aux, align=ALIGN):
+    """Element offsets of the library's packed layout (see pf12_tensors)."""
+    p, k, m = (np.asarray(a, np.int64) for a in (n_pao, n_pno, n_aux))
+    out = {}
+    for name, sz in (("pm", p * m), ("mm", m * m), ("pk", p * k), ("kk", k * k)):
+        padded = (sz + align - 1) // align * align
+        off = np.zeros(len(sz), np.int64)
+        if len(sz) > 1:
+            off[1:] = np.cumsum(padded)[:-1]
+        out["off_" + name] = off
+        out["len_" + name] = int(padded.sum()) if len(sz) else 0
+    return out
+
+
+def input_bytes(n_pao, n_pno, n_aux):
+    p, k, m = (np.asarray(a, np.float64) for a in (n_pao, n_pno, n_aux))
+    return 8.0 * (4 * p * m + 2 * m * m + p * k + k * k)
+
+
+def plan_batches(n_pao, n_pno, n_aux, budget_bytes):
+    """Contiguous [begin, end) ranges of pairs with inputs <= budget_bytes each."""
+    per = input_bytes(n_pao, n_pno, n_aux)
+    if len(per) and per.max() > budget_bytes:
+        raise ValueError("one pair alone exceeds the batch budget")
+    out, beg, acc = [], 0, 0.0
+    for P, b in enumerate(per):
+        if acc + b > budget_bytes and P > beg:
+            out.append((beg, P))
+            beg, acc = P, 0.0
+        acc += b
+    if beg < len(per):
+        out.append((beg, len(per)))
+    return out
+
+
+class StreamedPairF12:
+    """Runs the pair-F12 path batch by batch.
+
+    producer(begin, end, tensors, layout) must fill the packed device tensors
+    (keys Agi, Agj, Afi, Afj, Jg, Jf, Q, T) for pairs [begin, end) in the given
+    layout.  grad_consumer(begin, end, grads, layout), when given, receives the
+    batch's gradients (same packed layout) before the buffers are reused."""
+
+    def __init__(self, precision="mixed_fp32", budget_bytes=48e9, tuner_cache=None):
+        self.precision = precision
+        self.budget = float(budget_bytes)
+        self.tuner_cache = tuner_cache
+
+    def run(self, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, producer, backward=False,
+            grad_consumer=None, dE=1.0):
+        n = len(pi)
+        batches = plan_batches(n_pao, n_pno, n_aux, self.budget)
+        lays = [packed_layout(n_pao[b:e], n_pno[b:e], n_aux[b:e]) for b, e in batches]
+        cap = {key: max([L[key] for L in lays] + [2]) for key in ("len_pm", "len_mm", "len_pk", "len_kk")}
+        dev = "cuda"
+        t = {x: torch.zeros(cap["len_pm"], dtype=torch.float64, device=dev) for x in ("Agi", "Agj", "Afi", "Afj")}
+        t.update({x: torch.zeros(cap["len_mm"], dtype=torch.float64, device=dev) for x in ("Jg", "Jf")})
+        t["Q"] = torch.zeros(cap["len_pk"], dtype=torch.float64, device=dev)
+        t["T"] = torch.zeros(cap["len_kk"], dtype=torch.float64, device=dev)
+        g = None
+        if backward:
+            g = {x: torch.zeros_like(t[x]) for x in ("Agi", "Agj", "Afi", "Afj", "Q", "T")}
+        e_pair = torch.empty((max(n, 1), 3), dtype=torch.float64, device=dev)
+        eng = PairF12(self.precision, tuner_cache=self.tuner_cache)
+        totals, status = [], np.zeros(n, np.int32)
+        for (b, e), lay in zip(batches, lays):
+            producer(b, e, t, lay)
+            eng.upload_pairs(n_orb, orb_kind, pi[b:e], pj[b:e], n_pao[b:e], n_pno[b:e], n_aux[b:e],
+                             t, lay)
+            eng.fit()
+            Eb, _ = eng.energy(e_pair[b:e], check=False)
+            totals.append(Eb)
+            status[b:e] = eng.pair_status()
+            if backward:
+                eng.backward(dE, g)
+                if grad_consumer is not None:
+                    grad_consumer(b, e, g, lay)
+        torch.cuda.synchronize()
+        E = 0.0
+        for x in totals:
+            E += x
+        self.stats = eng.stats()
+        eng.close()
+        self.batches = batches
+        return E, e_pair[:n], status

@@ -1,0 +1,30 @@
+"""Host logic of the pair-streamed executor: packed layout and batch plan."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from paper_2008_03237_gb300.stream import input_bytes, packed_layout, plan_batches
+
+
+def test_packed_layout_matches_generator_layout():
+    wl = S.custom(6, 1, 3, (10, 50), ("uniform", 2, 9), (5, 70))
+    a = packed_layout(wl.n_pao, wl.n_pno, wl.n_aux)
+    b = S.packed_offsets(wl)
+    for key in a:
+        assert np.array_equal(np.asarray(a[key]), np.asarray(b[key])), key
+    assert all(int(o) % 32 == 0 for key in ("off_pm", "off_mm", "off_pk", "off_kk") for o in a[key])
+
+
+def test_plan_batches_covers_list_within_budget():
+    wl = S.lattice_quartet()
+    per = input_bytes(wl.n_pao, wl.n_pno, wl.n_aux)
+    budget = 40e9
+    batches = plan_batches(wl.n_pao, wl.n_pno, wl.n_aux, budget)
+    assert batches[0][0] == 0 and batches[-1][1] == wl.n_pairs
+    for (b0, e0), (b1, _) in zip(batches, batches[1:]):
+        assert e0 == b1
+    for b, e in batches:
+        assert per[b:e].sum() <= budget
+    assert per.sum() > 800e9 and len(batches) >= 20
+    with pytest.raises(ValueError):
+        plan_batches(wl.n_pao, wl.n_pno, wl.n_aux, per.max() / 2)
