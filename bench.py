@@ -55,6 +55,8 @@ def parse():
                     help="pair-streamed run: inputs drawn on the device batch by batch "
                          "(workloads larger than HBM); 0 = inputs resident")
     ap.add_argument("--backward", action="store_true", help="streamed run: adjoint per batch too")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="force a forward kernel variant instead of autotuning (profiling)")
     return ap.parse_args()
 
 
@@ -204,7 +206,8 @@ def run_ours(args, rank, world, local_rank):
     device.fill(wl, t, lay)
 
     def make(prec):
-        eng = pf.PairF12(prec)
+        var = args.variant if (args.variant is not None and (prec != "fp64" or args.variant < 2)) else None
+        eng = pf.PairF12(prec, variant=var)
         eng.upload_pairs(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
         return eng
 
@@ -389,8 +392,9 @@ def main():
         "gpu_launches": 2 * args.steps,
         "E_total_raw": o["E"], "pairs_failed": o["status_bad"],
         "autotuner": {"variant": o["stats"]["tile_config"],
-                      "variants": ["2 CTAs/SM", "3 CTAs/SM"],
-                      "sample_ms": o["stats"]["tune_ms"]},
+                      "variants": ["SIMT 2 CTAs/SM", "SIMT 3 CTAs/SM", "tcgen05 3 CTAs/SM"],
+                      "sample_ms": o["stats"]["tune_ms"],
+                      "ctas": o["stats"]["ctas_variant"]},
     }
     for key in ("fp64_mode", "error_vs_fp64", "e2e"):
         if key in o:

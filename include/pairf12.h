@@ -67,8 +67,10 @@ extern "C" {
  * FP64 Cholesky, solves and energy sums in every mode. */
 typedef enum {
   PF12_FP64 = 0,       /* everything FP64 (plain mode) */
-  PF12_MIXED_FP32 = 2  /* FP32 products, FP32 partial sums over 32-wide K chunks
-                          promoted to FP64 accumulators */
+  PF12_MIXED_FP32 = 2  /* FP32-class products with FP64 accumulation every 128 of K:
+                          FP32 FFMA, or tcgen05 split-TF32 (hi + lo, 3 products) for
+                          the projections and the J_f product when the autotuner picks
+                          the tensor-core variant */
 } pf12_precision;
 
 typedef struct pf12_ctx pf12_ctx; /* opaque, library-owned */
@@ -79,6 +81,8 @@ typedef struct {
   size_t workspace_bytes;  /* cap on library-owned device workspace; 0 = no cap */
   int deterministic;       /* reserved: energy sums are always fixed-order */
   const char* tuner_cache; /* path of the autotuner's cache file, or NULL (no cache) */
+  int force_variant;       /* -1: autotune; else the forward variant to use (see
+                              pf12_stats_t.tile_config); unavailable ones are refused */
 } pf12_opts;
 
 /* Packed ("plain mode") per-pair tensors.  Pair P's blocks start at element
@@ -118,9 +122,11 @@ typedef struct {
   int64_t n_pairs;
   int32_t n_ctas;        /* persistent CTAs of the fused pair kernel */
   int32_t launches_fit;  /* kernels launched by one pf12_fit */
-  int32_t tile_config;   /* autotuner choice: forward variant (0: 2 CTAs/SM, 1: 3 CTAs/SM) */
+  int32_t tile_config;   /* autotuner choice: forward variant (0: SIMT, 2 CTAs/SM; 1: SIMT,
+                            3 CTAs/SM; 2: tcgen05 tensor-core contractions, mixed mode only) */
   int32_t graph_used;    /* 1 when pf12_fit replays a captured CUDA graph */
-  double tune_ms[2];     /* autotuner timings of the variants on its sample (0 if not tuned) */
+  double tune_ms[3];     /* autotuner timings of the variants on its sample (0 if not run) */
+  int32_t ctas_variant[3]; /* persistent CTAs each variant launches (0: unavailable) */
 } pf12_stats_t;
 
 /* Create a context.  opts may be NULL (FP64, legacy stream, no cap). */

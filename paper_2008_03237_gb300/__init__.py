@@ -55,10 +55,14 @@ class PairF12:
     precision: "fp64" (plain mode) or "mixed_fp32".  FP64 Cholesky, solves and
     energy sums in both."""
 
-    def __init__(self, precision="fp64", workspace_bytes=0, stream=None, tuner_cache=None):
+    def __init__(self, precision="fp64", workspace_bytes=0, stream=None, tuner_cache=None,
+                 variant=None):
+        """variant: None = autotune, else 0 / 1 (SIMT, 2 / 3 CTAs per SM) or
+        2 (tcgen05 tensor-core contractions, mixed precision only)."""
         self._L = lib()
         self._cache = tuner_cache.encode() if tuner_cache else None
-        opts = _lib.Opts(_lib.PRECISION[precision], None, int(workspace_bytes), 1, self._cache)
+        opts = _lib.Opts(_lib.PRECISION[precision], None, int(workspace_bytes), 1, self._cache,
+                         -1 if variant is None else int(variant))
         h = ctypes.c_void_p()
         self._check(self._L.pf12_create(ctypes.byref(h), ctypes.byref(opts)), None)
         self._h = h
@@ -155,6 +159,7 @@ class PairF12:
         self._check(self._L.pf12_stats(self._h, ctypes.byref(s)))
         out = {n: getattr(s, n) for n, _ in _lib.Stats._fields_}
         out["tune_ms"] = list(s.tune_ms)
+        out["ctas_variant"] = list(s.ctas_variant)
         return out
 
 

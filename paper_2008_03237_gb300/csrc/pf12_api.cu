@@ -45,6 +45,7 @@ struct pf12_ctx {
 
   // autotuner: forward kernel variant (occupancy), its CTA counts, tuning sample
   int variant = -1;
+  int forced = -1;
   int n_ctas_v[pf12::kFwdVariants] = {};
   std::string tuner_cache;
   std::string tune_key;
@@ -125,6 +126,7 @@ pf12::FwdParams fwd_params(pf12_ctx* c) {
   f.work = c->d_work;
   f.ws_stride = c->ws_stride;
   f.counter = c->d_counter;
+  f.err = c->d_counter + 2;
   return f;
 }
 
@@ -145,6 +147,11 @@ int pf12_create(pf12_ctx** out, const pf12_opts* o) {
     c->stream = static_cast<cudaStream_t>(o->cuda_stream);
     c->ws_cap = o->workspace_bytes;
     if (o->tuner_cache) c->tuner_cache = o->tuner_cache;
+    if (o->force_variant >= pf12::kFwdVariants) {
+      delete c;
+      return PF12_ERR_UNSUPPORTED;
+    }
+    c->forced = o->force_variant;
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -270,7 +277,12 @@ int pf12_upload_pairs(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_
   }
   int64_t want = 1;
   for (int v = 0; v < pf12::kFwdVariants; ++v) {
-    const int bps = std::max(1, pf12::forward_blocks_per_sm(c->precision, v));
+    const int bps = pf12::forward_blocks_per_sm(c->precision, v);
+    cudaGetLastError();
+    if (bps <= 0) {       // variant not available for this precision
+      c->n_ctas_v[v] = 0;
+      continue;
+    }
     int64_t n_v = std::min<int64_t>(n_pairs, (int64_t)bps * c->n_sm);
     n_v = std::max<int64_t>(1, std::min(n_v, cap_f));
     c->n_ctas_v[v] = (int)n_v;
@@ -315,7 +327,7 @@ int pf12_upload_pairs(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_
   if (e == cudaSuccess) e = cudaMalloc(&c->d_dx, sizeof(double) * 2 * n);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int32_t) * n);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_out3, sizeof(double) * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, sizeof(int32_t) * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, sizeof(int32_t) * 4);
   if (e == cudaSuccess && n_pairs > 0) e = cudaMalloc(&c->d_work, sizeof(double) * work_doubles);
   if (e == cudaSuccess && n_s > 0) e = cudaMalloc(&c->d_desc_sample, sizeof(PairDesc) * n_s);
   if (e != cudaSuccess) {
@@ -333,6 +345,7 @@ int pf12_upload_pairs(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_
   c->n_sample = n_s;
   if (t && t->len_kk > 0) PF12_CUDA(c, cudaMemsetAsync(c->d_V, 0, sizeof(double) * t->len_kk, c->stream));
   PF12_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int32_t) * n, c->stream));
+  PF12_CUDA(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t) * 4, c->stream));
   PF12_CUDA(c, cudaMemsetAsync(c->d_epair, 0, sizeof(double) * 3 * n, c->stream));
   PF12_CUDA(c, cudaStreamSynchronize(c->stream));
   c->uploaded = true;
@@ -348,13 +361,19 @@ namespace {
 // fastest.  Results are cached per (GPU, precision, size signature) in the
 // optional tuner_cache file, one "key variant ms0 ms1" line per entry.
 int tune(pf12_ctx* c) {
+  if (c->forced >= 0) {
+    if (c->n_ctas_v[c->forced] <= 0)
+      return fail(c, PF12_ERR_UNSUPPORTED, "forced variant not available for this precision");
+    c->variant = c->forced;
+    return PF12_OK;
+  }
   if (!c->tuner_cache.empty()) {
     FILE* f = fopen(c->tuner_cache.c_str(), "r");
     if (f) {
       char key[512];
       int v = -1;
-      while (fscanf(f, "%511s %d %*f %*f", key, &v) == 2)
-        if (c->tune_key == key && v >= 0 && v < pf12::kFwdVariants) c->variant = v;
+      while (fscanf(f, "%511s %d %*f %*f %*f", key, &v) == 2)
+        if (c->tune_key == key && v >= 0 && v < pf12::kFwdVariants && c->n_ctas_v[v] > 0) c->variant = v;
       fclose(f);
     }
     if (c->variant >= 0) return PF12_OK;
@@ -368,6 +387,7 @@ int tune(pf12_ctx* c) {
   f.desc = c->d_desc_sample;
   int best = 0;
   for (int v = 0; v < pf12::kFwdVariants; ++v) {
+    if (c->n_ctas_v[v] <= 0) continue;
     f.n_pairs = 1;
     PF12_CUDA(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->stream));
     PF12_CUDA(c, pf12::launch_forward(f, c->precision, v, 1, c->stream));
@@ -386,7 +406,8 @@ int tune(pf12_ctx* c) {
   if (!c->tuner_cache.empty()) {
     FILE* fo = fopen(c->tuner_cache.c_str(), "a");
     if (fo) {
-      fprintf(fo, "%s %d %.3f %.3f\n", c->tune_key.c_str(), best, c->tune_ms[0], c->tune_ms[1]);
+      fprintf(fo, "%s %d %.3f %.3f %.3f\n", c->tune_key.c_str(), best, c->tune_ms[0], c->tune_ms[1],
+              c->tune_ms[2]);
       fclose(fo);
     }
   }
@@ -451,17 +472,22 @@ int pf12_energy(pf12_ctx* c, double* e_pair_dev, double* E_host) {
     return PF12_OK;
   }
   PF12_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
-  PF12_CUDA(c, pf12::launch_energy_total(c->d_epair, c->d_status, c->n_pairs, c->d_out3, c->stream));
+  PF12_CUDA(c, pf12::launch_energy_total(c->d_epair, c->d_status, c->n_pairs, c->d_counter + 2,
+                                         c->d_out3, c->stream));
   PF12_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   c->t_energy = true;
   if (e_pair_dev)
     PF12_CUDA(c, cudaMemcpyAsync(e_pair_dev, c->d_epair, sizeof(double) * 3 * c->n_pairs,
                                  cudaMemcpyDeviceToDevice, c->stream));
   if (!E_host) return PF12_OK;
-  double out3[3];
+  double out3[4];
   PF12_CUDA(c, cudaMemcpyAsync(out3, c->d_out3, sizeof out3, cudaMemcpyDeviceToHost, c->stream));
   PF12_CUDA(c, cudaStreamSynchronize(c->stream));
   *E_host = out3[0];
+  if (out3[3] != 0.0) {
+    *E_host = std::nan("");
+    return fail(c, PF12_ERR_TIMEOUT, "a bounded tensor-core wait expired; pairs after it were not evaluated");
+  }
   if (out3[1] > 0) {
     char buf[128];
     snprintf(buf, sizeof buf, "%lld pair(s) failed, first pair %lld", (long long)out3[1], (long long)out3[2]);
@@ -526,8 +552,10 @@ int pf12_stats(pf12_ctx* c, pf12_stats_t* s) {
   s->n_ctas = c->n_ctas;
   s->launches_fit = c->n_pairs > 0 ? 1 : 0;
   s->tile_config = c->variant;
-  s->tune_ms[0] = c->tune_ms[0];
-  s->tune_ms[1] = c->tune_ms[1];
+  for (int v = 0; v < 3; ++v) {
+    s->tune_ms[v] = c->tune_ms[v];
+    s->ctas_variant[v] = c->n_ctas_v[v];
+  }
   s->graph_used = c->graph_exec != nullptr;
   return PF12_OK;
 }

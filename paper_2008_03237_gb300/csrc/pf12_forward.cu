@@ -12,6 +12,7 @@
 #include "../../include/pairf12.h"
 #include "pf12_device.cuh"
 #include "pf12_internal.h"
+#include "pf12_tc.cuh"
 
 namespace pf12 {
 
@@ -119,14 +120,146 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_forward_kernel(FwdParams 
   }
 }
 
-// Tile/occupancy variants the autotuner chooses from: variant v runs MINB = 2 + v
-// CTAs per SM (more resident pairs per SM hide the serial phases of each
-// pair's factorisation; fewer leave more registers per thread).
+// Mixed-precision pair with the dense contractions on the tensor cores:
+// projections At^x = Q^T A^x and W = Ct_i J_f as tcgen05 split-TF32 GEMMs
+// (transposed tiles: m on the 128-row MMA axis, k on N), everything FP64
+// (Cholesky, solves, energy) unchanged.  Returns false after a bounded wait
+// expired (the pair gets status 3 and the kernel stops taking pairs).
+__device__ bool pair_forward_tc(const FwdParams& prm, const PairDesc& pd, double* ws, GemmSmem& gs,
+                                CholSmem& cs, double (*red)[kThreads / 32], tc::Stage& st,
+                                tc::Ctrl& ctrl, int* s_flag) {
+  const int tid = threadIdx.x;
+  const int p = pd.p, k = pd.k, m = pd.m;
+  const int64_t ld = (m + 3) / 4 * 4;
+  double* M = ws;
+  double* F = ws + (int64_t)(m + 2 * k) * ld;
+  const double* Jg = prm.Jg + pd.off_mm;
+  const double* Jf = prm.Jf + pd.off_mm;
+  const double* Q = prm.Q + pd.off_pk;
+  const double* T = prm.T + pd.off_kk;
+  for (int r = tid >> 5; r < m; r += kThreads / 32)
+    for (int c = tid & 31; c < m; c += 32) M[(int64_t)r * ld + c] = Jg[(int64_t)r * m + c];
+  const double* Asrc[4] = {prm.Agi + pd.off_pm, prm.Agj + pd.off_pm, prm.Afi + pd.off_pm,
+                           prm.Afj + pd.off_pm};
+  double* Adst[4] = {M + (int64_t)m * ld, M + (int64_t)(m + k) * ld, F, F + (int64_t)k * ld};
+#pragma unroll 1
+  for (int x = 0; x < 4; ++x)
+    if (!tc::gemm<true, true>(m, k, p, Asrc[x], m, Q, k, Adst[x], ld, 1.0, false, st, ctrl, s_flag))
+      return false;
+  __syncthreads();
+  const bool ok = chol_augmented(M, ld, m, m + 2 * k, cs, gs);
+  if (!ok) {
+    if (tid == 0) {
+      const double nan = __longlong_as_double(0x7ff8000000000000ll);
+      prm.status[pd.pair] = 1;
+      for (int q = 0; q < 3; ++q) prm.e_pair[3 * (int64_t)pd.pair + q] = nan;
+      prm.dx[2 * (int64_t)pd.pair] = nan;
+      prm.dx[2 * (int64_t)pd.pair + 1] = nan;
+    }
+    __syncthreads();
+    return true;
+  }
+  double* Ci = M + (int64_t)m * ld;
+  double* Cj = M + (int64_t)(m + k) * ld;
+  solve_right_lower(M, ld, m, Ci, ld, 2 * k, cs, gs);
+  double* Fi = F;
+  double* Fj = F + (int64_t)k * ld;
+  // F_i <- At^f_i - Ct_i J_f, computed as (J_f Ct_i^T)^T with J_f symmetric
+  if (!tc::gemm<false, false>(m, k, m, Jf, m, Ci, ld, Fi, ld, -1.0, true, st, ctrl, s_flag))
+    return false;
+  double* V = prm.V + pd.off_kk;
+  for (int r0 = 0; r0 < k; r0 += kTile)
+    for (int c0 = 0; c0 < k; c0 += kTile) {
+      cta_gemm_tile<float, false, true>(k, k, m, Fi, ld, Cj, ld, V, k, r0, c0, 1.0, false, gs);
+      cta_gemm_tile<float, false, true>(k, k, m, Ci, ld, Fj, ld, V, k, r0, c0, 1.0, true, gs);
+    }
+  __syncthreads();
+  double sd = 0.0, sx = 0.0;
+  for (int e = tid; e < k * k; e += kThreads) {
+    const int a = e / k, b = e - a * k;
+    const double v = V[e];
+    sd = fma(v, T[e], sd);
+    sx = fma(v, T[b * k + a], sx);
+  }
+  cta_sum2(sd, sx, red);
+  if (tid == 0) {
+    const int64_t P = pd.pair;
+    prm.e_pair[3 * P + 0] = pd.n_ab * (3.0 * sd + sx) / 8.0;
+    prm.e_pair[3 * P + 1] = pd.n_aa * (sd - sx) / 4.0;
+    prm.e_pair[3 * P + 2] = pd.n_bb * (sd - sx) / 4.0;
+    prm.dx[2 * P] = sd;
+    prm.dx[2 * P + 1] = sx;
+    prm.status[P] = (isfinite(sd) && isfinite(sx)) ? 0 : 2;
+  }
+  return true;
+}
+
+// shared memory of the tensor-core variant: the staging tiles share space with
+// the SIMT GEMM and Cholesky buffers (never live at the same time)
+constexpr size_t kTcUnion = sizeof(tc::Stage) > sizeof(GemmSmem) + sizeof(CholSmem)
+                                ? sizeof(tc::Stage)
+                                : sizeof(GemmSmem) + sizeof(CholSmem);
+constexpr size_t kTcSmem = kTcUnion + sizeof(tc::Ctrl) + 2 * (kThreads / 32) * sizeof(double) + 64;
+
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) pair_forward_tc_kernel(FwdParams prm) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  tc::Stage& st = *reinterpret_cast<tc::Stage*>(smem);
+  GemmSmem& gs = *reinterpret_cast<GemmSmem*>(smem);
+  CholSmem& cs = *reinterpret_cast<CholSmem*>(smem + sizeof(GemmSmem));
+  unsigned char* tail = smem + kTcUnion;
+  tc::Ctrl& ctrl = *reinterpret_cast<tc::Ctrl*>(tail);
+  double (*red)[kThreads / 32] = reinterpret_cast<double (*)[kThreads / 32]>(tail + sizeof(tc::Ctrl));
+  long long* s_slot = reinterpret_cast<long long*>(tail + sizeof(tc::Ctrl) + 2 * (kThreads / 32) * sizeof(double));
+  int* s_flag = reinterpret_cast<int*>(s_slot + 1);
+  if (threadIdx.x == 0) *s_flag = 0;
+  tc::setup(ctrl);
+  double* ws = prm.work + (int64_t)blockIdx.x * prm.ws_stride;
+  for (;;) {
+    if (threadIdx.x == 0) *s_slot = (*prm.err != 0) ? prm.n_pairs : atomicAdd(prm.counter, 1);
+    __syncthreads();
+    const long long slot = *s_slot;
+    __syncthreads();
+    if (slot >= prm.n_pairs) break;
+    const PairDesc pd = prm.desc[slot];
+    if (!pair_forward_tc(prm, pd, ws, gs, cs, red, st, ctrl, s_flag)) {
+      if (threadIdx.x == 0) {
+        prm.status[pd.pair] = 3;
+        atomicExch(prm.err, 1);
+      }
+      break;
+    }
+    __syncthreads();
+  }
+  tc::teardown(ctrl);
+}
+
+// Tile/occupancy variants the autotuner chooses from: variant 0 / 1 run the
+// SIMT kernel at MINB = 2 / 3 CTAs per SM (more resident pairs per SM hide the
+// serial phases of each pair's factorisation; fewer leave more registers per
+// thread); variant 2 (mixed precision only) is the tensor-core kernel at 3.
+static cudaError_t tc_attr() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(pair_forward_tc_kernel<3>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  // prefer the largest shared-memory carveout so that three 66 KB CTAs fit per SM
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pair_forward_tc_kernel<3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
 cudaError_t launch_forward(const FwdParams& prm, int precision, int variant, int n_ctas,
                            cudaStream_t s) {
   if (precision == 0) {
     if (variant == 1) pair_forward_kernel<double, 3><<<n_ctas, kThreads, 0, s>>>(prm);
     else pair_forward_kernel<double, 2><<<n_ctas, kThreads, 0, s>>>(prm);
+  } else if (variant == 2) {
+    cudaError_t e = tc_attr();
+    if (e != cudaSuccess) return e;
+    pair_forward_tc_kernel<3><<<n_ctas, kThreads, kTcSmem, s>>>(prm);
   } else {
     if (variant == 1) pair_forward_kernel<float, 3><<<n_ctas, kThreads, 0, s>>>(prm);
     else pair_forward_kernel<float, 2><<<n_ctas, kThreads, 0, s>>>(prm);
@@ -139,8 +272,27 @@ int forward_blocks_per_sm(int precision, int variant) {
   if (precision == 0) {
     if (variant == 1)
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_kernel<double, 3>, kThreads, 0);
-    else
+    else if (variant == 0)
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_kernel<double, 2>, kThreads, 0);
+  } else if (variant == 2) {
+    if (tc_attr() != cudaSuccess) return 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_tc_kernel<3>, kThreads, kTcSmem);
+    // resource model (registers, shared memory with the per-CTA reserve,
+    // threads); the runtime's answer for this dynamic-smem kernel can be lower
+    cudaFuncAttributes fa{};
+    int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0, reserve = 0;
+    if (cudaFuncGetAttributes(&fa, pair_forward_tc_kernel<3>) == cudaSuccess &&
+        cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess) {
+      const int by_regs = regs_sm / std::max(1, fa.numRegs * kThreads);
+      const int by_smem = smem_sm / (int)(fa.sharedSizeBytes + kTcSmem + reserve);
+      const int by_thr = thr_sm / kThreads;
+      n = std::max(n, std::min(by_regs, std::min(by_smem, by_thr)));
+    }
+    n = std::min(n, 4);  // 4 x 128 TMEM columns per SM at most
   } else {
     if (variant == 1)
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_kernel<float, 3>, kThreads, 0);
@@ -155,7 +307,7 @@ int forward_blocks_per_sm(int precision, int variant) {
 // non-OK pair or -1).
 __global__ void __launch_bounds__(1024) energy_total_kernel(const double* e_pair,
                                                             const int32_t* status, int64_t n,
-                                                            double* out3) {
+                                                            const int32_t* err, double* out3) {
   __shared__ double s_sum[1024];
   __shared__ long long s_bad[1024];
   __shared__ long long s_first[1024];
@@ -188,12 +340,13 @@ __global__ void __launch_bounds__(1024) energy_total_kernel(const double* e_pair
     out3[0] = s_sum[0];
     out3[1] = (double)s_bad[0];
     out3[2] = (double)s_first[0];
+    out3[3] = (err && *err) ? 1.0 : 0.0;
   }
 }
 
 cudaError_t launch_energy_total(const double* e_pair, const int32_t* status, int64_t n_pairs,
-                                double* out3, cudaStream_t s) {
-  energy_total_kernel<<<1, 1024, 0, s>>>(e_pair, status, n_pairs, out3);
+                                const int32_t* err, double* out3, cudaStream_t s) {
+  energy_total_kernel<<<1, 1024, 0, s>>>(e_pair, status, n_pairs, err, out3);
   return cudaGetLastError();
 }
 
@@ -342,7 +495,7 @@ extern "C" int pf12_energy_noalloc(int32_t n_orb, const int8_t* kind, int64_t n_
   f.counter = reinterpret_cast<int32_t*>(base);
   if (launch_forward(f, precision, 0, (int)n_ctas, s) != cudaSuccess) return PF12_ERR_CUDA;
   double* out3 = reinterpret_cast<double*>(base + off_out3);
-  if (launch_energy_total(e_pair_dev, f.status, n_pairs, out3, s) != cudaSuccess) return PF12_ERR_CUDA;
+  if (launch_energy_total(e_pair_dev, f.status, n_pairs, nullptr, out3, s) != cudaSuccess) return PF12_ERR_CUDA;
   double h3[3] = {0, 0, 0};
   if (cudaMemcpyAsync(h3, out3, sizeof h3, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PF12_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PF12_ERR_CUDA;

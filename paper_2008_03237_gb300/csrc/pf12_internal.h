@@ -31,6 +31,7 @@ struct FwdParams {
   double* work;       // n_ctas * ws_stride doubles
   int64_t ws_stride;  // doubles per CTA
   int32_t* counter;   // work-queue head, zeroed before each launch
+  int32_t* err;       // set when a bounded device wait expired (zeroed at upload)
 };
 
 struct BwdParams {
@@ -53,12 +54,12 @@ inline int64_t bwd_ws(int p, int k, int m) {
   return (int64_t)(m + 6 * k) * ld + 2 * (int64_t)k * ldk + 64;
 }
 
-constexpr int kFwdVariants = 2;
+constexpr int kFwdVariants = 3;
 cudaError_t launch_forward(const FwdParams& prm, int precision, int variant, int n_ctas,
                            cudaStream_t s);
 cudaError_t launch_backward(const BwdParams& prm, int precision, int n_ctas, cudaStream_t s);
 cudaError_t launch_energy_total(const double* e_pair, const int32_t* status, int64_t n_pairs,
-                                double* out3, cudaStream_t s);
+                                const int32_t* err, double* out3, cudaStream_t s);
 int forward_blocks_per_sm(int precision, int variant);
 int backward_blocks_per_sm(int precision);
 

@@ -32,11 +32,12 @@ def upload_host(wl, host=None):
     return t, lay
 
 
-def run(wl, precision="fp64", t=None, lay=None, want_V=True, want_grad=False, dE=1.0):
+def run(wl, precision="fp64", t=None, lay=None, want_V=True, want_grad=False, dE=1.0,
+        variant=None):
     import paper_2008_03237_gb300 as pf
     if t is None:
         t, lay = upload_host(wl)
-    eng = pf.PairF12(precision)
+    eng = pf.PairF12(precision, variant=variant)
     eng.upload_pairs(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
     eng.fit()
     E, e_pair = eng.energy()

@@ -43,19 +43,21 @@ def _check_fp64(wl, r, ref):
     assert abs(r["E"] - ref["E"]) <= 1e-10 * max(1.0, abs(ref["E"]))
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("make", [S.tiny, _mini, _edge])
-def test_forward_fp64(built, make):
+def test_forward_fp64(built, make, variant):
     wl = make()
     ref = O.run(wl, want_V=True)
-    r = run(wl, "fp64")
+    r = run(wl, "fp64", variant=variant)
     _check_fp64(wl, r, ref)
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("make", [S.tiny, _mini, _edge])
-def test_forward_mixed(built, make):
+def test_forward_mixed(built, make, variant):
     wl = make()
     ref = O.run(wl)
-    r = run(wl, "mixed_fp32", want_V=False)
+    r = run(wl, "mixed_fp32", want_V=False, variant=variant)
     rel = np.abs(r["e_pair"] - ref["e_pair"]).max() / np.abs(ref["e_pair"]).max()
     assert rel <= 1e-5, rel
     err = normalised_error(r["E"] - ref["E"], ref["sum_abs"], wl.n_orb)
@@ -115,6 +117,17 @@ def test_not_spd_pair_is_reported(built):
     ref = O.run(wl, pairs=[P for P in range(wl.n_pairs) if P != bad])
     assert np.isnan(e[bad]).all()
     assert np.abs(np.delete(e, bad, axis=0) - ref["e_pair"]).max() <= 1e-10
+
+
+def test_unavailable_variant_is_refused(built):
+    import paper_2008_03237_gb300 as pf
+    wl = S.tiny()
+    t, lay = upload_host(wl)
+    eng = pf.PairF12("fp64", variant=2)      # tensor-core kernel exists in mixed mode only
+    eng.upload_pairs(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
+    with pytest.raises(pf.Pf12Error) as ei:
+        eng.fit()
+    assert ei.value.code == -7
 
 
 def test_invalid_arguments(built):
