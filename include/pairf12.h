@@ -191,6 +191,56 @@ const char* pf12_last_error(const pf12_ctx* ctx);
 /* Release the context's workspace, graph and metadata. */
 void pf12_destroy(pf12_ctx* ctx);
 
+/* Gather mode ("pair-extended SparseMaps", Sec. "F12 integral
+ * transformations"): the three-index factors exist once per occupied orbital
+ * o on its pair-extended domain (PAOs of all pairs of o x auxiliary functions
+ * of all pairs of o), and every pair sieves its rows and columns out of the
+ * blocks of i and j on the device.  J_g, J_f, Q, T stay packed per pair.
+ *   Bg, Bf (device): per-orbital blocks, orbital o at element offset
+ *     off_orb[o], P_o rows x ld_o columns (row-major, ld_o >= M_o), 16-byte
+ *     aligned base; len_orb elements in each buffer
+ *   off_orb, ext_pao (P_o), ext_aux (M_o), ext_ld (ld_o): host, n_orb
+ *   map_pao (host): per pair 2p row indices, first into orbital i's block,
+ *     then into j's, each run strictly increasing; pair P's at off_map_pao[P]
+ *   map_aux (host): per pair 2m column indices, same convention
+ * The library copies the maps to the device.  Gradients come back per orbital
+ * block through pf12_backward_gather. */
+typedef struct {
+  const double* Bg;
+  const double* Bf;
+  const int64_t* off_orb;
+  const int32_t* ext_pao;
+  const int32_t* ext_aux;
+  const int32_t* ext_ld;
+  int64_t len_orb;
+  const int32_t* map_pao;
+  const int32_t* map_aux;
+  const int64_t* off_map_pao;
+  const int64_t* off_map_aux;
+  int64_t len_map_pao, len_map_aux;
+  const double* Jg;
+  const double* Jf;
+  const double* Q;
+  const double* T;
+  const int64_t* off_mm;
+  const int64_t* off_pk;
+  const int64_t* off_kk;
+  int64_t len_mm, len_pk, len_kk;
+} pf12_gather_tensors;
+
+/* As pf12_upload_pairs, with the factors given in gather mode. */
+int pf12_upload_pairs_gather(pf12_ctx* ctx, int32_t n_orb, const int8_t* orb_kind,
+                             int64_t n_pairs, const int32_t* pi, const int32_t* pj,
+                             const int32_t* n_pao, const int32_t* n_pno, const int32_t* n_aux,
+                             const pf12_gather_tensors* g);
+
+/* Adjoint in gather mode: per-pair factor gradients (computed as in
+ * pf12_backward) are summed into the per-orbital blocks dBg, dBf (layout of
+ * Bg, Bf; overwritten) in pair-list order, so the result is deterministic.
+ * dQ, dT as in pf12_backward.  Any pointer may be NULL to skip it. */
+int pf12_backward_gather(pf12_ctx* ctx, double dE, double* dBg, double* dBf, double* dQ,
+                         double* dT);
+
 /* Allocation-free forward pass: steps 1-6 for every pair in one call, with
  * no cudaMalloc, cudaFree or other allocating call.  The paper has no
  * counterpart; this entry point exists for callers that cannot allocate

@@ -117,6 +117,52 @@ class PairF12:
         self.n_pairs = n
         self.len_kk = tt.len_kk
 
+    def upload_pairs_gather(self, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, blocks, orbitals,
+                            maps, tensors, offsets):
+        """Gather mode.  blocks: dict Bg, Bf (packed per-orbital float64 CUDA
+        tensors); orbitals: dict off_orb, ext_pao, ext_aux, ext_ld (host);
+        maps: dict map_pao, map_aux, off_map_pao, off_map_aux (host);
+        tensors: Jg, Jf, Q, T (packed, CUDA); offsets: off_mm, off_pk, off_kk."""
+        self._stream()
+        kind = np.ascontiguousarray(np.asarray(orb_kind, dtype=np.int8))
+        meta = [_i32(pi), _i32(pj), _i32(n_pao), _i32(n_pno), _i32(n_aux)]
+        orb = {"off_orb": _i64(orbitals["off_orb"]), "ext_pao": _i32(orbitals["ext_pao"]),
+               "ext_aux": _i32(orbitals["ext_aux"]), "ext_ld": _i32(orbitals["ext_ld"])}
+        mp = {"map_pao": _i32(maps["map_pao"]), "map_aux": _i32(maps["map_aux"]),
+              "off_map_pao": _i64(maps["off_map_pao"]), "off_map_aux": _i64(maps["off_map_aux"])}
+        offs = {n: _i64(offsets[n]) for n in ("off_mm", "off_pk", "off_kk")}
+        g = _lib.GatherTensors()
+        g.Bg, g.Bf = _dev(blocks["Bg"], "Bg"), _dev(blocks["Bf"], "Bf")
+        g.off_orb = _ptr(orb["off_orb"], ctypes.c_int64)
+        for n in ("ext_pao", "ext_aux", "ext_ld"):
+            setattr(g, n, _ptr(orb[n], ctypes.c_int32))
+        g.len_orb = blocks["Bg"].numel()
+        g.map_pao, g.map_aux = _ptr(mp["map_pao"], ctypes.c_int32), _ptr(mp["map_aux"], ctypes.c_int32)
+        g.off_map_pao = _ptr(mp["off_map_pao"], ctypes.c_int64)
+        g.off_map_aux = _ptr(mp["off_map_aux"], ctypes.c_int64)
+        g.len_map_pao, g.len_map_aux = mp["map_pao"].size, mp["map_aux"].size
+        for n in ("Jg", "Jf", "Q", "T"):
+            setattr(g, n, _dev(tensors[n], n))
+        for n in offs:
+            setattr(g, n, _ptr(offs[n], ctypes.c_int64))
+        g.len_mm, g.len_pk, g.len_kk = (tensors["Jg"].numel(), tensors["Q"].numel(),
+                                        tensors["T"].numel())
+        n = len(meta[0])
+        self._check(self._L.pf12_upload_pairs_gather(
+            self._h, int(n_orb), _ptr(kind, ctypes.c_int8), n,
+            *[_ptr(a, ctypes.c_int32) for a in meta], ctypes.byref(g)))
+        self._keep = (blocks, orb, mp, tensors, offs, meta, kind)
+        self.n_pairs = n
+        self.len_kk = g.len_kk
+
+    def backward_gather(self, dE=1.0, grads=None):
+        """Gather mode: dE * dE_F12/d{Bg, Bf} (per-orbital blocks), dQ, dT."""
+        self._stream()
+        g = grads or {}
+        args = [_dev(g.get(n), n) for n in ("Bg", "Bf", "Q", "T")]
+        self._check(self._L.pf12_backward_gather(self._h, float(dE), *args))
+        return g
+
     def fit(self):
         self._stream()
         self._check(self._L.pf12_fit(self._h))

@@ -28,6 +28,16 @@ class Tensors(ctypes.Structure):
                [(n, ctypes.c_int64) for n in ("len_pm", "len_mm", "len_pk", "len_kk")]
 
 
+class GatherTensors(ctypes.Structure):
+    _fields_ = [("Bg", ctypes.c_void_p), ("Bf", ctypes.c_void_p), ("off_orb", c_i64p),
+                ("ext_pao", c_i32p), ("ext_aux", c_i32p), ("ext_ld", c_i32p), ("len_orb", ctypes.c_int64),
+                ("map_pao", c_i32p), ("map_aux", c_i32p), ("off_map_pao", c_i64p),
+                ("off_map_aux", c_i64p), ("len_map_pao", ctypes.c_int64), ("len_map_aux", ctypes.c_int64),
+                ("Jg", ctypes.c_void_p), ("Jf", ctypes.c_void_p), ("Q", ctypes.c_void_p),
+                ("T", ctypes.c_void_p), ("off_mm", c_i64p), ("off_pk", c_i64p), ("off_kk", c_i64p),
+                ("len_mm", ctypes.c_int64), ("len_pk", ctypes.c_int64), ("len_kk", ctypes.c_int64)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("ms_fit", ctypes.c_double), ("ms_energy", ctypes.c_double),
                 ("ms_backward", ctypes.c_double), ("flops_fp64", ctypes.c_double),
@@ -53,6 +63,10 @@ SIGNATURES = {
     "pf12_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "pf12_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "pf12_destroy": (None, [ctypes.c_void_p]),
+    "pf12_upload_pairs_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, c_i8p,
+                                                ctypes.c_int64, c_i32p, c_i32p, c_i32p, c_i32p,
+                                                c_i32p, ctypes.POINTER(GatherTensors)]),
+    "pf12_backward_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double] + [ctypes.c_void_p] * 4),
     "pf12_energy_noalloc": (ctypes.c_int, [ctypes.c_int32, c_i8p, ctypes.c_int64, c_i32p, c_i32p,
                                            c_i32p, c_i32p, c_i32p, ctypes.POINTER(Tensors),
                                            ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,

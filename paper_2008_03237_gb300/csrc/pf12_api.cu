@@ -53,6 +53,21 @@ struct pf12_ctx {
   PairDesc* d_desc_sample = nullptr;
   int64_t n_sample = 0;
 
+  // gather mode
+  bool gather = false;
+  int32_t n_orb = 0;
+  std::vector<int64_t> g_off_pm;   // library-computed packed offsets of per-pair gradient blocks
+  int64_t g_len_pm = 0, g_len_orb = 0;
+  const double *g_Bg = nullptr, *g_Bf = nullptr;
+  pf12::GatherDesc* d_gdesc = nullptr;
+  PairDesc* d_desc_by_pair = nullptr;
+  int32_t *d_map_pao = nullptr, *d_map_aux = nullptr;
+  int64_t* d_orb_ptr = nullptr;
+  int32_t* d_orb_list = nullptr;
+  int64_t* d_off_orb = nullptr;
+  int32_t* d_ld_orb = nullptr;
+  double* d_dA = nullptr;          // 4 x g_len_pm, allocated by the first gather backward
+
   // graph of the forward launch
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -82,6 +97,24 @@ int cuda_fail(pf12_ctx* c, cudaError_t e, const char* where) {
 
 void free_pairs(pf12_ctx* c) {
   cudaFree(c->d_desc);
+  cudaFree(c->d_gdesc);
+  cudaFree(c->d_desc_by_pair);
+  cudaFree(c->d_map_pao);
+  cudaFree(c->d_map_aux);
+  cudaFree(c->d_orb_ptr);
+  cudaFree(c->d_orb_list);
+  cudaFree(c->d_off_orb);
+  cudaFree(c->d_ld_orb);
+  cudaFree(c->d_dA);
+  c->d_gdesc = nullptr;
+  c->d_desc_by_pair = nullptr;
+  c->d_map_pao = c->d_map_aux = nullptr;
+  c->d_orb_ptr = nullptr;
+  c->d_orb_list = nullptr;
+  c->d_off_orb = nullptr;
+  c->d_ld_orb = nullptr;
+  c->d_dA = nullptr;
+  c->gather = false;
   cudaFree(c->d_desc_sample);
   c->d_desc_sample = nullptr;
   c->n_sample = 0;
@@ -127,6 +160,13 @@ pf12::FwdParams fwd_params(pf12_ctx* c) {
   f.ws_stride = c->ws_stride;
   f.counter = c->d_counter;
   f.err = c->d_counter + 2;
+  if (c->gather) {
+    f.gdesc = c->d_gdesc;
+    f.Bg = c->g_Bg;
+    f.Bf = c->g_Bf;
+    f.map_pao = c->d_map_pao;
+    f.map_aux = c->d_map_aux;
+  }
   return f;
 }
 
@@ -172,15 +212,50 @@ int pf12_set_stream(pf12_ctx* c, void* s) {
   return PF12_OK;
 }
 
-int pf12_upload_pairs(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_pairs,
-                      const int32_t* pi, const int32_t* pj, const int32_t* n_pao,
-                      const int32_t* n_pno, const int32_t* n_aux, const pf12_tensors* t) {
+static int upload_impl(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_pairs,
+                       const int32_t* pi, const int32_t* pj, const int32_t* n_pao,
+                       const int32_t* n_pno, const int32_t* n_aux, const pf12_tensors* t_in,
+                       const pf12_gather_tensors* g) {
   if (!c) return PF12_ERR_INVALID_ARG;
   free_pairs(c);
   if (n_pairs < 0 || n_orb < 0) return fail(c, PF12_ERR_INVALID_ARG, "negative count");
-  if (n_pairs > 0 && (!kind || !pi || !pj || !n_pao || !n_pno || !n_aux || !t))
+  if (n_pairs > 0 && (!kind || !pi || !pj || !n_pao || !n_pno || !n_aux || (!t_in && !g)))
     return fail(c, PF12_ERR_INVALID_ARG, "null metadata pointer");
-  if (n_pairs > 0) {
+  pf12_tensors tg{};
+  const pf12_tensors* t = t_in;
+  if (g && n_pairs > 0) {
+    // gather mode: factors come from per-orbital blocks; per-pair gradient
+    // blocks (backward) use a library-computed packed layout
+    const double* ptrs[6] = {g->Bg, g->Bf, g->Jg, g->Jf, g->Q, g->T};
+    for (const double* p : ptrs)
+      if (!p || !aligned16(p)) return fail(c, PF12_ERR_INVALID_ARG, "tensor pointer null or not 16-byte aligned");
+    if (!g->off_orb || !g->ext_pao || !g->ext_aux || !g->ext_ld || !g->map_pao || !g->map_aux ||
+        !g->off_map_pao || !g->off_map_aux || !g->off_mm || !g->off_pk || !g->off_kk)
+      return fail(c, PF12_ERR_INVALID_ARG, "null gather-mode array");
+    for (int32_t o = 0; o < n_orb; ++o)
+      if (g->off_orb[o] < 0 || g->ext_pao[o] < 0 || g->ext_aux[o] < 0 || g->ext_ld[o] < g->ext_aux[o] ||
+          g->off_orb[o] + (int64_t)g->ext_pao[o] * g->ext_ld[o] > g->len_orb)
+        return fail(c, PF12_ERR_INVALID_ARG, "orbital block outside Bg/Bf or ld < M");
+    c->g_off_pm.assign(n_pairs, 0);
+    int64_t acc = 0;
+    for (int64_t P = 0; P < n_pairs; ++P) {
+      c->g_off_pm[P] = acc;
+      acc += ((int64_t)std::max(n_pao[P], 0) * std::max(n_aux[P], 0) + 31) / 32 * 32;
+    }
+    tg.Jg = g->Jg;
+    tg.Jf = g->Jf;
+    tg.Q = g->Q;
+    tg.T = g->T;
+    tg.off_pm = c->g_off_pm.data();
+    tg.off_mm = g->off_mm;
+    tg.off_pk = g->off_pk;
+    tg.off_kk = g->off_kk;
+    tg.len_pm = acc;
+    tg.len_mm = g->len_mm;
+    tg.len_pk = g->len_pk;
+    tg.len_kk = g->len_kk;
+    t = &tg;
+  } else if (n_pairs > 0) {
     const double* ptrs[8] = {t->Ag_i, t->Ag_j, t->Af_i, t->Af_j, t->Jg, t->Jf, t->Q, t->T};
     for (const double* p : ptrs)
       if (!p || !aligned16(p)) return fail(c, PF12_ERR_INVALID_ARG, "tensor pointer null or not 16-byte aligned");
@@ -189,6 +264,8 @@ int pf12_upload_pairs(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_
   }
   for (int32_t o = 0; o < n_orb; ++o)
     if (kind[o] != 0 && kind[o] != 1) return fail(c, PF12_ERR_INVALID_ARG, "orb_kind must be 0 or 1");
+  const bool gm = g != nullptr;
+  std::vector<pf12::GatherDesc> gdesc(gm ? n_pairs : 0);
 
   std::vector<PairDesc> desc(n_pairs);
   std::vector<double> cost(n_pairs);
@@ -244,10 +321,39 @@ int pf12_upload_pairs(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_
     f64 += c64;
     fmix += cmix;
     bytes += 8.0 * (4.0 * dp * dm + 2.0 * dm * dm + dp * dk + dk * dk);
-    max_fwd = std::max(max_fwd, pf12::fwd_ws(p, k, m));
-    max_bwd = std::max(max_bwd, pf12::bwd_ws(p, k, m));
+    max_fwd = std::max(max_fwd, pf12::fwd_ws(p, k, m, gm));
+    max_bwd = std::max(max_bwd, pf12::bwd_ws(p, k, m, gm));
     c->off_kk[P] = offs[3];
     c->pk[P] = k;
+    if (gm) {
+      // maps: in range for the two orbitals' blocks and strictly increasing
+      const int64_t op = g->off_map_pao[P], oa = g->off_map_aux[P];
+      if (op < 0 || oa < 0 || op + 2 * (int64_t)p > g->len_map_pao || oa + 2 * (int64_t)m > g->len_map_aux) {
+        snprintf(buf, sizeof buf, "pair %lld: index map outside its array", (long long)P);
+        return fail(c, PF12_ERR_INVALID_ARG, buf);
+      }
+      const int32_t orb[2] = {i, j};
+      for (int side = 0; side < 2; ++side) {
+        const int32_t* rows = g->map_pao + op + (int64_t)side * p;
+        const int32_t* cols = g->map_aux + oa + (int64_t)side * m;
+        bool okm = true;
+        for (int r = 0; r < p; ++r)
+          okm &= rows[r] >= 0 && rows[r] < g->ext_pao[orb[side]] && (r == 0 || rows[r] > rows[r - 1]);
+        for (int q = 0; q < m; ++q)
+          okm &= cols[q] >= 0 && cols[q] < g->ext_aux[orb[side]] && (q == 0 || cols[q] > cols[q - 1]);
+        if (!okm) {
+          snprintf(buf, sizeof buf, "pair %lld: map out of range or not strictly increasing", (long long)P);
+          return fail(c, PF12_ERR_INVALID_ARG, buf);
+        }
+      }
+      pf12::GatherDesc& gd = gdesc[P];
+      gd.off_i = g->off_orb[i];
+      gd.off_j = g->off_orb[j];
+      gd.map_pao = op;
+      gd.map_aux = oa;
+      gd.ld_i = g->ext_ld[i];
+      gd.ld_j = g->ext_ld[j];
+    }
   }
   // longest-processing-time order for the persistent queue (ties: list order)
   std::vector<int64_t> order(n_pairs);
@@ -256,7 +362,7 @@ int pf12_upload_pairs(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_
   std::vector<PairDesc> sorted(n_pairs);
   for (int64_t s = 0; s < n_pairs; ++s) sorted[s] = desc[order[s]];
 
-  c->t = *t;
+  if (t) c->t = *t;
   c->n_pairs = n_pairs;
   c->flops64 = f64 + (c->precision == PF12_FP64 ? fmix : 0.0);
   c->flops_mix = fmix;
@@ -347,9 +453,68 @@ int pf12_upload_pairs(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_
   PF12_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int32_t) * n, c->stream));
   PF12_CUDA(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t) * 4, c->stream));
   PF12_CUDA(c, cudaMemsetAsync(c->d_epair, 0, sizeof(double) * 3 * n, c->stream));
+  if (gm && n_pairs > 0) {
+    // device copies of the maps, descriptors and the per-orbital scatter lists
+    std::vector<int64_t> orb_ptr(n_orb + 1, 0);
+    for (int64_t P = 0; P < n_pairs; ++P) {
+      ++orb_ptr[pi[P] + 1];
+      ++orb_ptr[pj[P] + 1];
+    }
+    for (int32_t o = 0; o < n_orb; ++o) orb_ptr[o + 1] += orb_ptr[o];
+    std::vector<int32_t> orb_list(2 * n_pairs);
+    std::vector<int64_t> fill(orb_ptr.begin(), orb_ptr.end() - 1);
+    for (int64_t P = 0; P < n_pairs; ++P) {
+      orb_list[fill[pi[P]]++] = (int32_t)(2 * P);
+      orb_list[fill[pj[P]]++] = (int32_t)(2 * P + 1);
+    }
+    std::vector<int64_t> off_orb(g->off_orb, g->off_orb + n_orb);
+    std::vector<int32_t> ld_orb(g->ext_ld, g->ext_ld + n_orb);
+    cudaError_t e2 = cudaSuccess;
+    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_gdesc, sizeof(pf12::GatherDesc) * n_pairs);
+    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_desc_by_pair, sizeof(PairDesc) * n_pairs);
+    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_map_pao, sizeof(int32_t) * std::max<int64_t>(g->len_map_pao, 1));
+    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_map_aux, sizeof(int32_t) * std::max<int64_t>(g->len_map_aux, 1));
+    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_orb_ptr, sizeof(int64_t) * (n_orb + 1));
+    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_orb_list, sizeof(int32_t) * 2 * n_pairs);
+    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_off_orb, sizeof(int64_t) * std::max(n_orb, 1));
+    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_ld_orb, sizeof(int32_t) * std::max(n_orb, 1));
+    if (e2 != cudaSuccess) {
+      cudaGetLastError();
+      free_pairs(c);
+      return fail(c, PF12_ERR_OOM, std::string("device allocation: ") + cudaGetErrorString(e2));
+    }
+    PF12_CUDA(c, cudaMemcpyAsync(c->d_gdesc, gdesc.data(), sizeof(pf12::GatherDesc) * n_pairs, cudaMemcpyHostToDevice, c->stream));
+    PF12_CUDA(c, cudaMemcpyAsync(c->d_desc_by_pair, desc.data(), sizeof(PairDesc) * n_pairs, cudaMemcpyHostToDevice, c->stream));
+    PF12_CUDA(c, cudaMemcpyAsync(c->d_map_pao, g->map_pao, sizeof(int32_t) * g->len_map_pao, cudaMemcpyHostToDevice, c->stream));
+    PF12_CUDA(c, cudaMemcpyAsync(c->d_map_aux, g->map_aux, sizeof(int32_t) * g->len_map_aux, cudaMemcpyHostToDevice, c->stream));
+    PF12_CUDA(c, cudaMemcpyAsync(c->d_orb_ptr, orb_ptr.data(), sizeof(int64_t) * (n_orb + 1), cudaMemcpyHostToDevice, c->stream));
+    PF12_CUDA(c, cudaMemcpyAsync(c->d_orb_list, orb_list.data(), sizeof(int32_t) * 2 * n_pairs, cudaMemcpyHostToDevice, c->stream));
+    PF12_CUDA(c, cudaMemcpyAsync(c->d_off_orb, off_orb.data(), sizeof(int64_t) * n_orb, cudaMemcpyHostToDevice, c->stream));
+    PF12_CUDA(c, cudaMemcpyAsync(c->d_ld_orb, ld_orb.data(), sizeof(int32_t) * n_orb, cudaMemcpyHostToDevice, c->stream));
+    c->gather = true;
+    c->n_orb = n_orb;
+    c->g_Bg = g->Bg;
+    c->g_Bf = g->Bf;
+    c->g_len_pm = t->len_pm;
+    c->g_len_orb = g->len_orb;
+  }
   PF12_CUDA(c, cudaStreamSynchronize(c->stream));
   c->uploaded = true;
   return PF12_OK;
+}
+
+int pf12_upload_pairs(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_pairs,
+                      const int32_t* pi, const int32_t* pj, const int32_t* n_pao,
+                      const int32_t* n_pno, const int32_t* n_aux, const pf12_tensors* t) {
+  return upload_impl(c, n_orb, kind, n_pairs, pi, pj, n_pao, n_pno, n_aux, t, nullptr);
+}
+
+int pf12_upload_pairs_gather(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_pairs,
+                             const int32_t* pi, const int32_t* pj, const int32_t* n_pao,
+                             const int32_t* n_pno, const int32_t* n_aux,
+                             const pf12_gather_tensors* g) {
+  if (!g) return fail(c, PF12_ERR_INVALID_ARG, "null gather tensors");
+  return upload_impl(c, n_orb, kind, n_pairs, pi, pj, n_pao, n_pno, n_aux, nullptr, g);
 }
 
 }  // extern "C"
@@ -504,6 +669,7 @@ int pf12_backward(pf12_ctx* c, double dE, double* dAgi, double* dAgj, double* dA
                   double* dQ, double* dT) {
   if (!c) return PF12_ERR_INVALID_ARG;
   if (!c->uploaded) return fail(c, PF12_ERR_INVALID_ARG, "pf12_backward before pf12_upload_pairs");
+  if (c->gather) return fail(c, PF12_ERR_INVALID_ARG, "gather mode: use pf12_backward_gather");
   if (c->n_pairs == 0) return PF12_OK;
   pf12::BwdParams b{};
   b.f = fwd_params(c);
@@ -522,6 +688,61 @@ int pf12_backward(pf12_ctx* c, double dE, double* dAgi, double* dAgj, double* dA
   PF12_CUDA(c, cudaEventRecord(c->ev[4], c->stream));
   PF12_CUDA(c, cudaMemsetAsync(c->d_counter + 1, 0, sizeof(int32_t), c->stream));
   PF12_CUDA(c, pf12::launch_backward(b, c->precision, c->n_ctas_bwd, c->stream));
+  PF12_CUDA(c, cudaEventRecord(c->ev[5], c->stream));
+  c->t_bwd = true;
+  return PF12_OK;
+}
+
+int pf12_backward_gather(pf12_ctx* c, double dE, double* dBg, double* dBf, double* dQ, double* dT) {
+  if (!c) return PF12_ERR_INVALID_ARG;
+  if (!c->uploaded || !c->gather)
+    return fail(c, PF12_ERR_INVALID_ARG, "pf12_backward_gather needs pf12_upload_pairs_gather");
+  if (c->n_pairs == 0) return PF12_OK;
+  const void* outs[4] = {dBg, dBf, dQ, dT};
+  for (const void* p : outs)
+    if (p && !aligned16(p)) return fail(c, PF12_ERR_INVALID_ARG, "gradient pointer not 16-byte aligned");
+  const bool want_b = dBg || dBf;
+  if (want_b && !c->d_dA) {
+    cudaError_t e = cudaMalloc(&c->d_dA, sizeof(double) * 4 * (size_t)std::max<int64_t>(c->g_len_pm, 1));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->d_dA = nullptr;
+      return fail(c, PF12_ERR_OOM, "per-pair gradient scratch");
+    }
+  }
+  pf12::BwdParams b{};
+  b.f = fwd_params(c);
+  b.f.work = c->d_work;
+  b.f.ws_stride = c->ws_stride_bwd;
+  b.dE = dE;
+  if (want_b) {
+    b.dAgi = c->d_dA;
+    b.dAgj = c->d_dA + c->g_len_pm;
+    b.dAfi = c->d_dA + 2 * c->g_len_pm;
+    b.dAfj = c->d_dA + 3 * c->g_len_pm;
+  }
+  b.dQ = dQ;
+  b.dT = dT;
+  PF12_CUDA(c, cudaEventRecord(c->ev[4], c->stream));
+  PF12_CUDA(c, cudaMemsetAsync(c->d_counter + 1, 0, sizeof(int32_t), c->stream));
+  PF12_CUDA(c, pf12::launch_backward(b, c->precision, c->n_ctas_bwd, c->stream));
+  if (want_b) {
+    // both orbital gradients are produced; a NULL one goes to a throwaway copy
+    double* gb = dBg;
+    double* gf = dBf;
+    double* tmp = nullptr;
+    if (!gb || !gf) {
+      PF12_CUDA(c, cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(double) * std::max<int64_t>(c->g_len_orb, 1), c->stream));
+      if (!gb) gb = tmp;
+      if (!gf) gf = tmp;
+    }
+    PF12_CUDA(c, cudaMemsetAsync(gb, 0, sizeof(double) * c->g_len_orb, c->stream));
+    if (gf != gb) PF12_CUDA(c, cudaMemsetAsync(gf, 0, sizeof(double) * c->g_len_orb, c->stream));
+    PF12_CUDA(c, pf12::launch_scatter(b.dAgi, b.dAgj, b.dAfi, b.dAfj, c->d_desc_by_pair, c->d_gdesc,
+                                      c->d_map_pao, c->d_map_aux, c->d_orb_ptr, c->d_orb_list,
+                                      c->d_off_orb, c->d_ld_orb, c->n_orb, gb, gf, c->stream));
+    if (tmp) PF12_CUDA(c, cudaFreeAsync(tmp, c->stream));
+  }
   PF12_CUDA(c, cudaEventRecord(c->ev[5], c->stream));
   c->t_bwd = true;
   return PF12_OK;

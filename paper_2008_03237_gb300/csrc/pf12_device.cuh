@@ -337,6 +337,32 @@ __device__ __forceinline__ void solve_right_lowerT(const double* L, int64_t ld, 
 }
 
 // ---------------------------------------------------------------------------
+// Gather mode: sieve pair P's four factor blocks out of the per-orbital
+// pair-extended blocks (Sec. "F12 integral transformations") into dst as
+// packed p x m blocks [Ag_i, Ag_j, Af_i, Af_j].  Rows go to warps, columns to
+// lanes: the column indices are runs of whole atoms, so reads are coalesced.
+__device__ __forceinline__ void sieve_pair(const FwdParams& prm, const PairDesc& pd, double* dst) {
+  const GatherDesc g = prm.gdesc[pd.pair];
+  const int p = pd.p, m = pd.m;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t* rows[2] = {prm.map_pao + g.map_pao, prm.map_pao + g.map_pao + p};
+  const int32_t* cols[2] = {prm.map_aux + g.map_aux, prm.map_aux + g.map_aux + m};
+  const int64_t off[2] = {g.off_i, g.off_j};
+  const int32_t ldo[2] = {g.ld_i, g.ld_j};
+#pragma unroll 1
+  for (int x = 0; x < 4; ++x) {
+    const int side = x & 1;
+    const double* src = (x < 2 ? prm.Bg : prm.Bf) + off[side];
+    double* out = dst + (int64_t)x * p * m;
+    for (int r = warp; r < p; r += kThreads / 32) {
+      const double* row = src + (int64_t)rows[side][r] * ldo[side];
+      for (int c = lane; c < m; c += 32) out[(int64_t)r * m + c] = row[cols[side][c]];
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // Fixed-order CTA sum of two per-thread values (deterministic for a fixed
 // kThreads): butterfly within each warp, then warps in index order.
 __device__ __forceinline__ void cta_sum2(double& a, double& b, double (*red)[kThreads / 32]) {

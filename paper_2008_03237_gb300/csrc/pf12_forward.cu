@@ -38,9 +38,16 @@ __device__ void pair_forward(const FwdParams& prm, const PairDesc& pd, double* w
   for (int r = tid >> 5; r < m; r += kThreads / 32)
     for (int c = tid & 31; c < m; c += 32) M[(int64_t)r * ld + c] = Jg[(int64_t)r * m + c];
 
-  // S1': At^x = Q^T A^x  (k x m), A(a, mu) = Q[mu * k + a]
+  // S1: packed factors, or (gather mode) the pair's blocks sieved out of the
+  // per-orbital pair-extended blocks into the slab
   const double* Asrc[4] = {prm.Agi + pd.off_pm, prm.Agj + pd.off_pm, prm.Afi + pd.off_pm,
                            prm.Afj + pd.off_pm};
+  if (prm.gdesc) {
+    double* G = ws + fwd_sieve_off(k, m);
+    sieve_pair(prm, pd, G);
+    for (int x = 0; x < 4; ++x) Asrc[x] = G + (int64_t)x * p * m;
+  }
+  // S1': At^x = Q^T A^x  (k x m), A(a, mu) = Q[mu * k + a]
   double* Adst[4] = {M + (int64_t)m * ld, M + (int64_t)(m + k) * ld, F, F + (int64_t)k * ld};
 #pragma unroll 1
   for (int x = 0; x < 4; ++x)
@@ -141,6 +148,11 @@ __device__ bool pair_forward_tc(const FwdParams& prm, const PairDesc& pd, double
     for (int c = tid & 31; c < m; c += 32) M[(int64_t)r * ld + c] = Jg[(int64_t)r * m + c];
   const double* Asrc[4] = {prm.Agi + pd.off_pm, prm.Agj + pd.off_pm, prm.Afi + pd.off_pm,
                            prm.Afj + pd.off_pm};
+  if (prm.gdesc) {
+    double* G = ws + fwd_sieve_off(k, m);
+    sieve_pair(prm, pd, G);
+    for (int x = 0; x < 4; ++x) Asrc[x] = G + (int64_t)x * p * m;
+  }
   double* Adst[4] = {M + (int64_t)m * ld, M + (int64_t)(m + k) * ld, F, F + (int64_t)k * ld};
 #pragma unroll 1
   for (int x = 0; x < 4; ++x)

@@ -20,6 +20,13 @@ struct PairDesc {
   int8_t n_ab, n_aa, n_bb, pad;            // spin-case multiplicities
 };
 
+// Gather mode: where pair P's factors live inside the per-orbital blocks.
+struct GatherDesc {
+  int64_t off_i, off_j;      // element offsets of orbital i's and j's blocks
+  int64_t map_pao, map_aux;  // offsets of the pair's 2p row / 2m column indices
+  int32_t ld_i, ld_j;        // row strides of those blocks
+};
+
 struct FwdParams {
   const double *Agi, *Agj, *Afi, *Afj, *Jg, *Jf, *Q, *T;
   const PairDesc* desc;
@@ -32,6 +39,10 @@ struct FwdParams {
   int64_t ws_stride;  // doubles per CTA
   int32_t* counter;   // work-queue head, zeroed before each launch
   int32_t* err;       // set when a bounded device wait expired (zeroed at upload)
+  // gather mode (null in packed mode): A blocks are sieved from per-orbital blocks
+  const GatherDesc* gdesc;   // indexed by the caller's pair index
+  const double *Bg, *Bf;     // per-orbital extended blocks (Coulomb, F12)
+  const int32_t *map_pao, *map_aux;
 };
 
 struct BwdParams {
@@ -42,16 +53,27 @@ struct BwdParams {
 
 // per-CTA workspace (doubles) for a pair of sizes (p, k, m), forward / backward
 inline int64_t ld_of(int m) { return (int64_t)((m + 3) / 4 * 4); }
-inline int64_t fwd_ws(int p, int k, int m) {
+inline int64_t fwd_ws(int p, int k, int m, bool gather = false) {
   int64_t ld = ld_of(m);
-  return (int64_t)(m + 2 * k) * ld + 2 * (int64_t)k * ld + 64;
+  return (int64_t)(m + 2 * k) * ld + 2 * (int64_t)k * ld + 64 +
+         (gather ? 4 * (int64_t)p * m + 64 : 0);
 }
-inline int64_t bwd_ws(int p, int k, int m) {
+// offset of the sieved A blocks (4 x p x m) inside a forward slab
+inline __host__ __device__ int64_t fwd_sieve_off(int k, int m) {
+  const int64_t ld = (m + 3) / 4 * 4;
+  return ((int64_t)(m + 2 * k) * ld + 2 * (int64_t)k * ld + 31) / 32 * 32;
+}
+inline int64_t bwd_ws(int p, int k, int m, bool gather = false) {
   int64_t ld = ld_of(m);
   int64_t ldk = (k + 3) / 4 * 4;
   // M = [J_g -> L; Ct_i; Ct_j] (m + 2k rows), F (2k rows: At^f, then H),
   // R (2k rows: At^f - Ct J_f, then Z^T), G_V and V (k x k each)
-  return (int64_t)(m + 6 * k) * ld + 2 * (int64_t)k * ldk + 64;
+  return (int64_t)(m + 6 * k) * ld + 2 * (int64_t)k * ldk + 64 +
+         (gather ? 4 * (int64_t)p * m + 64 : 0);
+}
+inline __host__ __device__ int64_t bwd_sieve_off(int k, int m) {
+  const int64_t ld = (m + 3) / 4 * 4, ldk = (k + 3) / 4 * 4;
+  return ((int64_t)(m + 6 * k) * ld + 2 * (int64_t)k * ldk + 31) / 32 * 32;
 }
 
 constexpr int kFwdVariants = 3;
@@ -61,6 +83,13 @@ cudaError_t launch_backward(const BwdParams& prm, int precision, int n_ctas, cud
 cudaError_t launch_energy_total(const double* e_pair, const int32_t* status, int64_t n_pairs,
                                 const int32_t* err, double* out3, cudaStream_t s);
 int forward_blocks_per_sm(int precision, int variant);
+// gather mode: adjoint scatter into per-orbital blocks (one CTA per orbital,
+// pairs in list order)
+cudaError_t launch_scatter(const double* dAgi, const double* dAgj, const double* dAfi,
+                           const double* dAfj, const PairDesc* desc_by_pair, const GatherDesc* gdesc,
+                           const int32_t* map_pao, const int32_t* map_aux, const int64_t* orb_ptr,
+                           const int32_t* orb_list, const int64_t* off_orb, const int32_t* ld_orb,
+                           int32_t n_orb, double* dBg, double* dBf, cudaStream_t s);
 int backward_blocks_per_sm(int precision);
 
 }  // namespace pf12
