@@ -72,6 +72,16 @@ struct pf12_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
 
+  // capacities (elements) of the device buffers: re-uploads reuse them and only
+  // grow, so a re-upload issues no cudaFree (which would synchronise the device
+  // and stall copies running on other streams)
+  size_t cap_desc = 0, cap_sample = 0, cap_V = 0, cap_ep = 0, cap_dx = 0, cap_st = 0, cap_work = 0, cap_gdesc = 0,
+         cap_dbp = 0, cap_mp = 0, cap_ma = 0, cap_optr = 0, cap_olist = 0, cap_oorb = 0,
+         cap_ld = 0, cap_dA = 0;
+  bool fixed_allocated = false;
+  std::string prev_key;      // tuning key of the previous upload (variant kept if equal)
+  int prev_variant = -1;
+
   // timers
   cudaEvent_t ev[6] = {};
   bool t_fit = false, t_energy = false, t_bwd = false;
@@ -95,47 +105,44 @@ int cuda_fail(pf12_ctx* c, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
+// Forget the pair list (buffers are kept for the next upload).
 void free_pairs(pf12_ctx* c) {
-  cudaFree(c->d_desc);
-  cudaFree(c->d_gdesc);
-  cudaFree(c->d_desc_by_pair);
-  cudaFree(c->d_map_pao);
-  cudaFree(c->d_map_aux);
-  cudaFree(c->d_orb_ptr);
-  cudaFree(c->d_orb_list);
-  cudaFree(c->d_off_orb);
-  cudaFree(c->d_ld_orb);
-  cudaFree(c->d_dA);
-  c->d_gdesc = nullptr;
-  c->d_desc_by_pair = nullptr;
-  c->d_map_pao = c->d_map_aux = nullptr;
-  c->d_orb_ptr = nullptr;
-  c->d_orb_list = nullptr;
-  c->d_off_orb = nullptr;
-  c->d_ld_orb = nullptr;
-  c->d_dA = nullptr;
-  c->gather = false;
-  cudaFree(c->d_desc_sample);
-  c->d_desc_sample = nullptr;
-  c->n_sample = 0;
-  c->variant = -1;
-  cudaFree(c->d_V);
-  cudaFree(c->d_epair);
-  cudaFree(c->d_dx);
-  cudaFree(c->d_status);
-  cudaFree(c->d_out3);
-  cudaFree(c->d_counter);
-  cudaFree(c->d_work);
-  c->d_desc = nullptr;
-  c->d_V = c->d_epair = c->d_dx = c->d_out3 = c->d_work = nullptr;
-  c->d_status = c->d_counter = nullptr;
-  c->work_bytes = 0;
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   c->graph_exec = nullptr;
   c->graph = nullptr;
+  if (c->variant >= 0) {
+    c->prev_key = c->tune_key;
+    c->prev_variant = c->variant;
+  }
+  c->variant = -1;
+  c->n_sample = 0;
+  c->gather = false;
   c->uploaded = c->fitted = false;
   c->n_pairs = 0;
+}
+
+void release_all(pf12_ctx* c) {
+  free_pairs(c);
+  void* ptrs[] = {c->d_desc, c->d_gdesc, c->d_desc_by_pair, c->d_map_pao, c->d_map_aux,
+                  c->d_orb_ptr, c->d_orb_list, c->d_off_orb, c->d_ld_orb, c->d_dA,
+                  c->d_desc_sample, c->d_V, c->d_epair, c->d_dx, c->d_status, c->d_out3,
+                  c->d_counter, c->d_work};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+template <typename T>
+cudaError_t grow(T*& p, size_t& cap, size_t count) {
+  count = std::max<size_t>(count, 1);
+  if (p && count <= cap) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), sizeof(T) * count);
+  if (e == cudaSuccess) cap = count;
+  else p = nullptr;
+  return e;
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -424,18 +431,26 @@ static int upload_impl(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n
     for (char& ch : c->tune_key)
       if (ch == ' ') ch = '_';
   }
+  if (c->forced < 0 && c->prev_variant >= 0 && c->prev_key == c->tune_key &&
+      c->n_ctas_v[c->prev_variant] > 0) {
+    c->variant = c->prev_variant;     // same size signature as the last list: keep its tuning
+    c->n_ctas = c->n_ctas_v[c->variant];
+  }
 
   const size_t n = (size_t)std::max<int64_t>(n_pairs, 1);
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_desc, sizeof(PairDesc) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_V, sizeof(double) * (size_t)std::max<int64_t>(t ? t->len_kk : 0, 2));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_epair, sizeof(double) * 3 * n);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_dx, sizeof(double) * 2 * n);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int32_t) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_out3, sizeof(double) * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, sizeof(int32_t) * 4);
-  if (e == cudaSuccess && n_pairs > 0) e = cudaMalloc(&c->d_work, sizeof(double) * work_doubles);
-  if (e == cudaSuccess && n_s > 0) e = cudaMalloc(&c->d_desc_sample, sizeof(PairDesc) * n_s);
+  if (e == cudaSuccess) e = grow(c->d_desc, c->cap_desc, n);
+  if (e == cudaSuccess) e = grow(c->d_V, c->cap_V, (size_t)std::max<int64_t>(t ? t->len_kk : 0, 2));
+  if (e == cudaSuccess) e = grow(c->d_epair, c->cap_ep, 3 * n);
+  if (e == cudaSuccess) e = grow(c->d_dx, c->cap_dx, 2 * n);
+  if (e == cudaSuccess) e = grow(c->d_status, c->cap_st, n);
+  if (e == cudaSuccess && !c->fixed_allocated) {
+    e = cudaMalloc(&c->d_out3, sizeof(double) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) c->fixed_allocated = true;
+  }
+  if (e == cudaSuccess && n_pairs > 0) e = grow(c->d_work, c->cap_work, work_doubles);
+  if (e == cudaSuccess && n_s > 0) e = grow(c->d_desc_sample, c->cap_sample, (size_t)n_s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_pairs(c);
@@ -470,14 +485,14 @@ static int upload_impl(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n
     std::vector<int64_t> off_orb(g->off_orb, g->off_orb + n_orb);
     std::vector<int32_t> ld_orb(g->ext_ld, g->ext_ld + n_orb);
     cudaError_t e2 = cudaSuccess;
-    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_gdesc, sizeof(pf12::GatherDesc) * n_pairs);
-    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_desc_by_pair, sizeof(PairDesc) * n_pairs);
-    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_map_pao, sizeof(int32_t) * std::max<int64_t>(g->len_map_pao, 1));
-    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_map_aux, sizeof(int32_t) * std::max<int64_t>(g->len_map_aux, 1));
-    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_orb_ptr, sizeof(int64_t) * (n_orb + 1));
-    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_orb_list, sizeof(int32_t) * 2 * n_pairs);
-    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_off_orb, sizeof(int64_t) * std::max(n_orb, 1));
-    if (e2 == cudaSuccess) e2 = cudaMalloc(&c->d_ld_orb, sizeof(int32_t) * std::max(n_orb, 1));
+    if (e2 == cudaSuccess) e2 = grow(c->d_gdesc, c->cap_gdesc, (size_t)n_pairs);
+    if (e2 == cudaSuccess) e2 = grow(c->d_desc_by_pair, c->cap_dbp, (size_t)n_pairs);
+    if (e2 == cudaSuccess) e2 = grow(c->d_map_pao, c->cap_mp, (size_t)g->len_map_pao);
+    if (e2 == cudaSuccess) e2 = grow(c->d_map_aux, c->cap_ma, (size_t)g->len_map_aux);
+    if (e2 == cudaSuccess) e2 = grow(c->d_orb_ptr, c->cap_optr, (size_t)n_orb + 1);
+    if (e2 == cudaSuccess) e2 = grow(c->d_orb_list, c->cap_olist, 2 * (size_t)n_pairs);
+    if (e2 == cudaSuccess) e2 = grow(c->d_off_orb, c->cap_oorb, (size_t)n_orb);
+    if (e2 == cudaSuccess) e2 = grow(c->d_ld_orb, c->cap_ld, (size_t)n_orb);
     if (e2 != cudaSuccess) {
       cudaGetLastError();
       free_pairs(c);
@@ -702,11 +717,10 @@ int pf12_backward_gather(pf12_ctx* c, double dE, double* dBg, double* dBf, doubl
   for (const void* p : outs)
     if (p && !aligned16(p)) return fail(c, PF12_ERR_INVALID_ARG, "gradient pointer not 16-byte aligned");
   const bool want_b = dBg || dBf;
-  if (want_b && !c->d_dA) {
-    cudaError_t e = cudaMalloc(&c->d_dA, sizeof(double) * 4 * (size_t)std::max<int64_t>(c->g_len_pm, 1));
+  if (want_b) {
+    cudaError_t e = grow(c->d_dA, c->cap_dA, 4 * (size_t)std::max<int64_t>(c->g_len_pm, 1));
     if (e != cudaSuccess) {
       cudaGetLastError();
-      c->d_dA = nullptr;
       return fail(c, PF12_ERR_OOM, "per-pair gradient scratch");
     }
   }
@@ -786,7 +800,7 @@ const char* pf12_last_error(const pf12_ctx* c) { return c ? c->err.c_str() : "nu
 void pf12_destroy(pf12_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
-  free_pairs(c);
+  release_all(c);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);

@@ -101,3 +101,68 @@ class StreamedPairF12:
         eng.close()
         self.batches = batches
         return E, e_pair[:n], status
+
+
+def run_from_host(eng_factory, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, host, layout,
+                  budget_bytes):
+    """End-to-end run from packed inputs in (pinned) host memory.
+
+    The pair list is cut into batches under budget_bytes; batch b + 1's slices
+    are copied host -> device on a separate stream into the other of two device
+    slots while batch b is fitted on the current stream, so copies overlap the
+    compute.  Returns (E, e_pair (device, n x 3), status)."""
+    n = len(pi)
+    batches = plan_batches(n_pao, n_pno, n_aux, budget_bytes)
+    kinds = {"Agi": "pm", "Agj": "pm", "Afi": "pm", "Afj": "pm", "Jg": "mm", "Jf": "mm",
+             "Q": "pk", "T": "kk"}
+    sizes = {"pm": np.asarray(n_pao, np.int64) * n_aux, "mm": np.asarray(n_aux, np.int64) ** 2,
+             "pk": np.asarray(n_pao, np.int64) * n_pno, "kk": np.asarray(n_pno, np.int64) ** 2}
+    ranges = []
+    for b, e in batches:
+        r = {}
+        for key in ("pm", "mm", "pk", "kk"):
+            off = layout["off_" + key]
+            r[key] = (int(off[b]), int(off[e - 1] + sizes[key][e - 1]))
+        ranges.append(r)
+    cap = {key: max(r[key][1] - r[key][0] for r in ranges) + 2 for key in ("pm", "mm", "pk", "kk")}
+    slots = [{x: torch.empty(cap[kinds[x]], dtype=torch.float64, device="cuda") for x in kinds}
+             for _ in range(2)]
+    copy_stream = torch.cuda.Stream()
+    compute = torch.cuda.current_stream()
+    copied = [torch.cuda.Event() for _ in batches]
+    done = [torch.cuda.Event() for _ in batches]
+
+    def issue(q):
+        slot = slots[q % 2]
+        with torch.cuda.stream(copy_stream):
+            if q >= 2:
+                copy_stream.wait_event(done[q - 2])
+            for x, key in kinds.items():
+                s0, s1 = ranges[q][key]
+                slot[x][:s1 - s0].copy_(host[x][s0:s1], non_blocking=True)
+            copied[q].record(copy_stream)
+
+    e_pair = torch.empty((max(n, 1), 3), dtype=torch.float64, device="cuda")
+    status = np.zeros(n, np.int32)
+    eng = eng_factory()
+    totals = []
+    issue(0)
+    for q, (b, e) in enumerate(batches):
+        if q + 1 < len(batches):
+            issue(q + 1)
+        compute.wait_event(copied[q])
+        lay_b = {"off_" + key: np.asarray(layout["off_" + key][b:e]) - ranges[q][key][0]
+                 for key in ("pm", "mm", "pk", "kk")}
+        eng.upload_pairs(n_orb, orb_kind, pi[b:e], pj[b:e], n_pao[b:e], n_pno[b:e], n_aux[b:e],
+                         slots[q % 2], lay_b)
+        eng.fit()
+        Eb, _ = eng.energy(e_pair[b:e], check=False)
+        totals.append(Eb)
+        status[b:e] = eng.pair_status()
+        done[q].record(compute)
+    torch.cuda.synchronize()
+    E = 0.0
+    for x in totals:
+        E += x
+    eng.close()
+    return E, e_pair[:n], status, len(batches)

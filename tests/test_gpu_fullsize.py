@@ -14,6 +14,16 @@ import synthetic as S
 from gpu_helpers import grad_blocks, normalised_error
 
 pytestmark = pytest.mark.gpu
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    """Oracle values of every pair, written by tests/golden/make_fullsize_oracle.py."""
+    import os
+    path = os.path.join(GOLDEN, f"{name}_oracle.npz")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not generated")
+    return np.load(path)
 
 
 @pytest.fixture(scope="module")
@@ -71,6 +81,9 @@ def test_c40h81_fp64_full_list(built):
     E, e = eng.energy()
     e = e.cpu().numpy()
     _properties(wl, e, E, eng.pair_status())
+    ref_all = _golden("c40h81")
+    assert np.abs(e - ref_all["e_pair"]).max() <= 1e-10           # every pair against the oracle
+    assert abs(E - float(ref_all["E"])) <= 1e-9
     V = eng.build_v().cpu().numpy()
     pairs = _sample(wl, 14, 1)
     ref = O.run(wl, pairs=pairs, want_V=True)
@@ -130,3 +143,6 @@ def test_c160h321_mixed_full_list(built):
         assert np.abs(e[P] - ref["e_pair"][n]).max() <= 1e-5 * scale, P
     sum_abs = float(np.abs(e64.sum(axis=1)).sum())
     assert normalised_error(E - E64, sum_abs, wl.n_orb) <= 1e-6
+    ref_all = _golden("c160h321")
+    assert np.abs(e64 - ref_all["e_pair"]).max() <= 1e-10         # FP64 path, every pair
+    assert normalised_error(E - float(ref_all["E"]), float(ref_all["sum_abs"]), wl.n_orb) <= 1e-6

@@ -82,3 +82,21 @@ def test_lattice_quartet_streamed_mixed_with_backward(built, tmp_path):
         assert np.abs(e[P] - ref["e_pair"][n]).max() <= 1e-5 * np.abs(ref["e_pair"][n]).max(), P
         for name, want in ref["grads"][n].items():
             assert np.abs(kept[P][name] - want).max() <= 2e-5 * np.abs(want).max(), (P, name)
+
+
+def test_host_pipelined_equals_resident(built, tmp_path):
+    """Inputs in pinned host memory, copied batch by batch on a second stream
+    while the previous batch is fitted: same pair energies as the resident run."""
+    import paper_2008_03237_gb300 as pf
+    from paper_2008_03237_gb300.stream import input_bytes, run_from_host
+    wl = S.custom(6, 2, 4, (30, 90), ("uniform", 3, 40), (40, 160), name="e2e-mini")
+    host, lay = S.packed_inputs(wl)
+    one = run(wl, "fp64", want_V=False)
+    pinned = {n: torch.from_numpy(v).pin_memory() for n, v in host.items()}
+    budget = input_bytes(wl.n_pao, wl.n_pno, wl.n_aux).sum() / 3.5
+    E, e, st, nb = run_from_host(lambda: pf.PairF12("fp64", tuner_cache=str(tmp_path / "t.txt")),
+                                 wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux,
+                                 pinned, lay, budget)
+    assert nb >= 3 and (st == 0).all()
+    assert np.array_equal(e.cpu().numpy(), one["e_pair"])
+    assert abs(E - one["E"]) <= 1e-12 * np.abs(one["e_pair"]).sum()
