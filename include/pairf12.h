@@ -67,10 +67,10 @@ extern "C" {
  * FP64 Cholesky, solves and energy sums in every mode. */
 typedef enum {
   PF12_FP64 = 0,       /* everything FP64 (plain mode) */
-  PF12_MIXED_FP32 = 2  /* FP32-class products with FP64 accumulation every 128 of K:
-                          FP32 FFMA, or tcgen05 split-TF32 (hi + lo, 3 products) for
-                          the projections and the J_f product when the autotuner picks
-                          the tensor-core variant */
+  PF12_MIXED_FP32 = 2  /* FP32-class products with FP64 accumulation: FP32 FFMA
+                          (promoted every 128 of K), or, when the autotuner picks the
+                          tensor-core variant, tcgen05 split-TF32 (hi + lo, 3 products)
+                          for the projections and the J_f product (promoted every 32) */
 } pf12_precision;
 
 typedef struct pf12_ctx pf12_ctx; /* opaque, library-owned */
@@ -127,6 +127,8 @@ typedef struct {
   int32_t graph_used;    /* 1 when pf12_fit replays a captured CUDA graph */
   double tune_ms[3];     /* autotuner timings of the variants on its sample (0 if not run) */
   int32_t ctas_variant[3]; /* persistent CTAs each variant launches (0: unavailable) */
+  int32_t bwd_variant;   /* adjoint variant (0: 2 CTAs/SM, 1: 3 CTAs/SM; -1 before tuning) */
+  double tune_bwd_ms[2]; /* adjoint tuner timings */
 } pf12_stats_t;
 
 /* Create a context.  opts may be NULL (FP64, legacy stream, no cap). */

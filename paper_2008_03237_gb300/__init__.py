@@ -206,6 +206,7 @@ class PairF12:
         out = {n: getattr(s, n) for n, _ in _lib.Stats._fields_}
         out["tune_ms"] = list(s.tune_ms)
         out["ctas_variant"] = list(s.ctas_variant)
+        out["tune_bwd_ms"] = list(s.tune_bwd_ms)
         return out
 
 

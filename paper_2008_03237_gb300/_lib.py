@@ -45,7 +45,8 @@ class Stats(ctypes.Structure):
                 ("n_pairs", ctypes.c_int64), ("n_ctas", ctypes.c_int32),
                 ("launches_fit", ctypes.c_int32), ("tile_config", ctypes.c_int32),
                 ("graph_used", ctypes.c_int32), ("tune_ms", ctypes.c_double * 3),
-                ("ctas_variant", ctypes.c_int32 * 3)]
+                ("ctas_variant", ctypes.c_int32 * 3), ("bwd_variant", ctypes.c_int32),
+                ("tune_bwd_ms", ctypes.c_double * 2)]
 
 
 # name -> (restype, argtypes); the same names as the C entry points

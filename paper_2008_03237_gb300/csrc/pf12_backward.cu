@@ -114,8 +114,8 @@ __device__ void pair_backward(const BwdParams& b, const PairDesc& pd, double* ws
   if (tid == 0) prm.status[pd.pair] = 0;
 }
 
-template <typename TC>
-__global__ void __launch_bounds__(kThreads, 2) pair_backward_kernel(BwdParams b) {
+template <typename TC, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) pair_backward_kernel(BwdParams b) {
   __shared__ GemmSmem gs;
   __shared__ CholSmem cs;
   __shared__ long long s_slot;
@@ -132,11 +132,17 @@ __global__ void __launch_bounds__(kThreads, 2) pair_backward_kernel(BwdParams b)
   }
 }
 
-cudaError_t launch_backward(const BwdParams& prm, int precision, int n_ctas, cudaStream_t s) {
-  if (precision == 0)
-    pair_backward_kernel<double><<<n_ctas, kThreads, 0, s>>>(prm);
-  else
-    pair_backward_kernel<float><<<n_ctas, kThreads, 0, s>>>(prm);
+// Adjoint variants: 0 / 1 = MINB 2 / 3 CTAs per SM (chosen by the tuner at the
+// first pf12_backward).
+cudaError_t launch_backward(const BwdParams& prm, int precision, int variant, int n_ctas,
+                            cudaStream_t s) {
+  if (precision == 0) {
+    if (variant == 1) pair_backward_kernel<double, 3><<<n_ctas, kThreads, 0, s>>>(prm);
+    else pair_backward_kernel<double, 2><<<n_ctas, kThreads, 0, s>>>(prm);
+  } else {
+    if (variant == 1) pair_backward_kernel<float, 3><<<n_ctas, kThreads, 0, s>>>(prm);
+    else pair_backward_kernel<float, 2><<<n_ctas, kThreads, 0, s>>>(prm);
+  }
   return cudaGetLastError();
 }
 
@@ -186,12 +192,19 @@ cudaError_t launch_scatter(const double* dAgi, const double* dAgj, const double*
   return cudaGetLastError();
 }
 
-int backward_blocks_per_sm(int precision) {
+int backward_blocks_per_sm(int precision, int variant) {
   int n = 0;
-  if (precision == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_backward_kernel<double>, kThreads, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_backward_kernel<float>, kThreads, 0);
+  if (precision == 0) {
+    if (variant == 1)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_backward_kernel<double, 3>, kThreads, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_backward_kernel<double, 2>, kThreads, 0);
+  } else {
+    if (variant == 1)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_backward_kernel<float, 3>, kThreads, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_backward_kernel<float, 2>, kThreads, 0);
+  }
   return n;
 }
 

@@ -79,7 +79,9 @@ inline __host__ __device__ int64_t bwd_sieve_off(int k, int m) {
 constexpr int kFwdVariants = 3;
 cudaError_t launch_forward(const FwdParams& prm, int precision, int variant, int n_ctas,
                            cudaStream_t s);
-cudaError_t launch_backward(const BwdParams& prm, int precision, int n_ctas, cudaStream_t s);
+constexpr int kBwdVariants = 2;
+cudaError_t launch_backward(const BwdParams& prm, int precision, int variant, int n_ctas,
+                            cudaStream_t s);
 cudaError_t launch_energy_total(const double* e_pair, const int32_t* status, int64_t n_pairs,
                                 const int32_t* err, double* out3, cudaStream_t s);
 int forward_blocks_per_sm(int precision, int variant);
@@ -90,6 +92,6 @@ cudaError_t launch_scatter(const double* dAgi, const double* dAgj, const double*
                            const int32_t* map_pao, const int32_t* map_aux, const int64_t* orb_ptr,
                            const int32_t* orb_list, const int64_t* off_orb, const int32_t* ld_orb,
                            int32_t n_orb, double* dBg, double* dBf, cudaStream_t s);
-int backward_blocks_per_sm(int precision);
+int backward_blocks_per_sm(int precision, int variant);
 
 }  // namespace pf12

@@ -9,9 +9,9 @@
 // and  B(n, t) = TB ? B[t * ldb + n] : B[n * ldb + t];
 // K is consumed in 32-wide chunks staged by all threads (FP64 -> FP32 -> tf32
 // hi/lo, canonical K-major layout without swizzle), one thread issues the
-// MMAs, a commit to an mbarrier signals completion, and every 128 of K the
+// MMAs, a commit to an mbarrier signals completion, and after every chunk the
 // FP32 accumulator is added into the FP64 output Out[n * ldo + r] (scaled by
-// alpha).  Every wait is bounded; on expiry the routine returns false.
+// alpha): short FP32 spans keep the accumulator's rounding bias small.  Every wait is bounded; on expiry the routine returns false.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -22,7 +22,7 @@ namespace tc {
 constexpr int kM = 128;        // rows per tile (TMEM lanes)
 constexpr int kNmax = 128;     // columns per tile (TMEM columns allocated)
 constexpr int kKC = 32;        // K chunk staged at once (4 MMA k-steps of 8)
-constexpr int kPromote = 4;    // chunks accumulated in TMEM before the FP64 add
+constexpr int kPromote = 1;    // chunks accumulated in TMEM before the FP64 add
 constexpr uint32_t kWaitLimit = 1u << 26;
 
 // shared-memory staging: A hi/lo (128 x 32 tf32) and B hi/lo (128 x 32 tf32)

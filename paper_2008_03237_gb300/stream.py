@@ -103,14 +103,16 @@ class StreamedPairF12:
         return E, e_pair[:n], status
 
 
-def run_from_host(eng_factory, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, host, layout,
+def run_from_host(eng, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, host, layout,
                   budget_bytes):
     """End-to-end run from packed inputs in (pinned) host memory.
 
     The pair list is cut into batches under budget_bytes; batch b + 1's slices
     are copied host -> device on a separate stream into the other of two device
     slots while batch b is fitted on the current stream, so copies overlap the
-    compute.  Returns (E, e_pair (device, n x 3), status)."""
+    compute.  eng is a PairF12 context, reused across calls (its device
+    buffers and tuned variant carry over).  Returns (E, e_pair (device,
+    n x 3), status, number of batches)."""
     n = len(pi)
     batches = plan_batches(n_pao, n_pno, n_aux, budget_bytes)
     kinds = {"Agi": "pm", "Agj": "pm", "Afi": "pm", "Afj": "pm", "Jg": "mm", "Jf": "mm",
@@ -144,7 +146,6 @@ def run_from_host(eng_factory, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, hos
 
     e_pair = torch.empty((max(n, 1), 3), dtype=torch.float64, device="cuda")
     status = np.zeros(n, np.int32)
-    eng = eng_factory()
     totals = []
     issue(0)
     for q, (b, e) in enumerate(batches):
@@ -164,5 +165,4 @@ def run_from_host(eng_factory, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, hos
     E = 0.0
     for x in totals:
         E += x
-    eng.close()
     return E, e_pair[:n], status, len(batches)

@@ -94,7 +94,7 @@ def test_host_pipelined_equals_resident(built, tmp_path):
     one = run(wl, "fp64", want_V=False)
     pinned = {n: torch.from_numpy(v).pin_memory() for n, v in host.items()}
     budget = input_bytes(wl.n_pao, wl.n_pno, wl.n_aux).sum() / 3.5
-    E, e, st, nb = run_from_host(lambda: pf.PairF12("fp64", tuner_cache=str(tmp_path / "t.txt")),
+    E, e, st, nb = run_from_host(pf.PairF12("fp64", tuner_cache=str(tmp_path / "t.txt")),
                                  wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux,
                                  pinned, lay, budget)
     assert nb >= 3 and (st == 0).all()
