@@ -83,6 +83,8 @@ typedef struct {
   const char* tuner_cache; /* path of the autotuner's cache file, or NULL (no cache) */
   int force_variant;       /* -1: autotune; else the forward variant to use (see
                               pf12_stats_t.tile_config); unavailable ones are refused */
+  int sieve_plain;         /* gather mode: 1 = sieve with plain loads; 0 = TMA tile::gather4
+                              loads when every orbital block starts and strides on 16 bytes */
 } pf12_opts;
 
 /* Packed ("plain mode") per-pair tensors.  Pair P's blocks start at element
@@ -128,6 +130,7 @@ typedef struct {
   double tune_ms[3];     /* autotuner timings of the variants on its sample (0 if not run) */
   int32_t ctas_variant[3]; /* persistent CTAs each variant launches (0: unavailable) */
   int32_t bwd_variant;   /* adjoint variant (0: 2 CTAs/SM, 1: 3 CTAs/SM; -1 before tuning) */
+  int32_t sieve_tma;     /* gather mode: 1 when the sieve uses TMA tile::gather4 loads */
   double tune_bwd_ms[2]; /* adjoint tuner timings */
 } pf12_stats_t;
 

@@ -19,7 +19,8 @@ c_dp = ctypes.POINTER(ctypes.c_double)
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("deterministic", ctypes.c_int),
-                ("tuner_cache", ctypes.c_char_p), ("force_variant", ctypes.c_int)]
+                ("tuner_cache", ctypes.c_char_p), ("force_variant", ctypes.c_int),
+                ("sieve_plain", ctypes.c_int)]
 
 
 class Tensors(ctypes.Structure):
@@ -46,7 +47,7 @@ class Stats(ctypes.Structure):
                 ("launches_fit", ctypes.c_int32), ("tile_config", ctypes.c_int32),
                 ("graph_used", ctypes.c_int32), ("tune_ms", ctypes.c_double * 3),
                 ("ctas_variant", ctypes.c_int32 * 3), ("bwd_variant", ctypes.c_int32),
-                ("tune_bwd_ms", ctypes.c_double * 2)]
+                ("sieve_tma", ctypes.c_int32), ("tune_bwd_ms", ctypes.c_double * 2)]
 
 
 # name -> (restype, argtypes); the same names as the C entry points

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/pairf12.h: argument checks, pair
 // metadata and cost-sorted work queue, workspace sizing, CUDA-graph capture of
 // the fused forward launch, deterministic energy total, timers.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -70,6 +71,10 @@ struct pf12_ctx {
   int64_t* d_off_orb = nullptr;
   int32_t* d_ld_orb = nullptr;
   double* d_dA = nullptr;          // 4 x g_len_pm, allocated by the first gather backward
+  unsigned char* d_tmaps = nullptr;  // 2 x n_orb TMA tensor maps (128 B each) of the orbital blocks
+  size_t cap_tmaps = 0;
+  bool use_tma = false;
+  bool sieve_plain = false;        // option: sieve with plain loads only
 
   // graph of the forward launch
   cudaGraph_t graph = nullptr;
@@ -131,7 +136,7 @@ void release_all(pf12_ctx* c) {
   void* ptrs[] = {c->d_desc, c->d_gdesc, c->d_desc_by_pair, c->d_map_pao, c->d_map_aux,
                   c->d_orb_ptr, c->d_orb_list, c->d_off_orb, c->d_ld_orb, c->d_dA,
                   c->d_desc_sample, c->d_V, c->d_epair, c->d_dx, c->d_status, c->d_out3,
-                  c->d_counter, c->d_work};
+                  c->d_counter, c->d_work, c->d_tmaps};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -172,6 +177,7 @@ pf12::FwdParams fwd_params(pf12_ctx* c) {
   f.counter = c->d_counter;
   f.err = c->d_counter + 2;
   if (c->gather) {
+    f.tmaps = c->use_tma ? c->d_tmaps : nullptr;
     f.gdesc = c->d_gdesc;
     f.Bg = c->g_Bg;
     f.Bf = c->g_Bf;
@@ -203,6 +209,7 @@ int pf12_create(pf12_ctx** out, const pf12_opts* o) {
       return PF12_ERR_UNSUPPORTED;
     }
     c->forced = o->force_variant;
+    c->sieve_plain = o->sieve_plain != 0;
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -364,6 +371,8 @@ static int upload_impl(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n
       gd.map_aux = oa;
       gd.ld_i = g->ext_ld[i];
       gd.ld_j = g->ext_ld[j];
+      gd.orb_i = i;
+      gd.orb_j = j;
     }
   }
   // longest-processing-time order for the persistent queue (ties: list order)
@@ -517,6 +526,52 @@ static int upload_impl(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n
     PF12_CUDA(c, cudaMemcpyAsync(c->d_orb_list, orb_list.data(), sizeof(int32_t) * 2 * n_pairs, cudaMemcpyHostToDevice, c->stream));
     PF12_CUDA(c, cudaMemcpyAsync(c->d_off_orb, off_orb.data(), sizeof(int64_t) * n_orb, cudaMemcpyHostToDevice, c->stream));
     PF12_CUDA(c, cudaMemcpyAsync(c->d_ld_orb, ld_orb.data(), sizeof(int32_t) * n_orb, cudaMemcpyHostToDevice, c->stream));
+    // TMA tensor maps of the orbital blocks for the gather4 sieve: rank 2,
+    // (ld_o columns, P_o rows), box 128 x 1; every block must start and stride
+    // on 16 bytes, else the sieve keeps plain loads
+    c->use_tma = false;
+    bool eligible = !c->sieve_plain;
+    for (int32_t o = 0; o < n_orb && eligible; ++o)
+      eligible = (g->off_orb[o] % 2 == 0) && (g->ext_ld[o] % 2 == 0);
+    using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    EncodeFn encode = nullptr;
+    if (eligible) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q{};
+      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                           &q) == cudaSuccess &&
+          q == cudaDriverEntryPointSuccess && fn)
+        encode = reinterpret_cast<EncodeFn>(fn);
+      cudaGetLastError();
+    }
+    if (encode) {
+      std::vector<CUtensorMap> maps(2 * (size_t)n_orb);
+      std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+      bool ok = true;
+      for (int32_t o = 0; o < n_orb && ok; ++o) {
+        if (g->ext_pao[o] <= 0 || g->ext_ld[o] <= 0) continue;   // orbital without pairs
+        const cuuint64_t dims[2] = {(cuuint64_t)g->ext_ld[o], (cuuint64_t)g->ext_pao[o]};
+        const cuuint64_t strides[1] = {(cuuint64_t)g->ext_ld[o] * sizeof(double)};
+        const cuuint32_t box[2] = {128, 1};
+        const cuuint32_t estr[2] = {1, 1};
+        const double* bases[2] = {g->Bg + g->off_orb[o], g->Bf + g->off_orb[o]};
+        for (int q2 = 0; q2 < 2 && ok; ++q2)
+          ok = encode(&maps[2 * o + q2], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                      const_cast<double*>(bases[q2]), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+               CUDA_SUCCESS;
+      }
+      if (ok && grow(c->d_tmaps, c->cap_tmaps, maps.size() * sizeof(CUtensorMap)) == cudaSuccess) {
+        PF12_CUDA(c, cudaMemcpyAsync(c->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap),
+                                     cudaMemcpyHostToDevice, c->stream));
+        c->use_tma = true;
+      }
+      cudaGetLastError();
+    }
     c->gather = true;
     c->n_orb = n_orb;
     c->g_Bg = g->Bg;
@@ -853,6 +908,7 @@ int pf12_stats(pf12_ctx* c, pf12_stats_t* s) {
     s->ctas_variant[v] = c->n_ctas_v[v];
   }
   s->bwd_variant = c->bwd_variant;
+  s->sieve_tma = c->gather && c->use_tma;
   for (int v = 0; v < 2; ++v) s->tune_bwd_ms[v] = c->tune_bwd_ms[v];
   s->graph_used = c->graph_exec != nullptr;
   return PF12_OK;

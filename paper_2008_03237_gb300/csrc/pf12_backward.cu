@@ -16,8 +16,8 @@
 namespace pf12 {
 
 template <typename TC>
-__device__ void pair_backward(const BwdParams& b, const PairDesc& pd, double* ws, GemmSmem& gs,
-                              CholSmem& cs) {
+__device__ bool pair_backward(const BwdParams& b, const PairDesc& pd, double* ws, GemmSmem& gs,
+                              CholSmem& cs, SieveCtl& sc, uint32_t& phase) {
   const FwdParams& prm = b.f;
   const int tid = threadIdx.x;
   const int p = pd.p, k = pd.k, m = pd.m;
@@ -38,7 +38,7 @@ __device__ void pair_backward(const BwdParams& b, const PairDesc& pd, double* ws
   const double* Afj = prm.Afj + pd.off_pm;
   if (prm.gdesc) {   // gather mode: the pair's factor blocks sieved into the slab
     double* G = ws + bwd_sieve_off(k, m);
-    sieve_pair(prm, pd, G);
+    if (!sieve_pair(prm, pd, G, gs, sc, phase)) return false;
     Agi = G;
     Agj = G + (int64_t)p * m;
     Afi = G + 2 * (int64_t)p * m;
@@ -54,7 +54,7 @@ __device__ void pair_backward(const BwdParams& b, const PairDesc& pd, double* ws
 
   if (!chol_augmented(M, ld, m, m + 2 * k, cs, gs)) {
     if (tid == 0) prm.status[pd.pair] = 1;
-    return;
+    return true;
   }
   double* Ci = M + (int64_t)m * ld;
   double* Cj = M + (int64_t)(m + k) * ld;
@@ -112,6 +112,7 @@ __device__ void pair_backward(const BwdParams& b, const PairDesc& pd, double* ws
     cta_gemm<TC, false, true>(p, k, m, Agj, m, H2, ld, dQ, k, 1.0, true, gs);
   }
   if (tid == 0) prm.status[pd.pair] = 0;
+  return true;
 }
 
 template <typename TC, int MINB>
@@ -119,15 +120,25 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_backward_kernel(BwdParams
   __shared__ GemmSmem gs;
   __shared__ CholSmem cs;
   __shared__ long long s_slot;
+  __shared__ SieveCtl sc;
+  uint32_t phase = 0;
+  if (b.f.gdesc) sieve_init(sc);
   double* ws = b.f.work + (int64_t)blockIdx.x * b.f.ws_stride;
   for (;;) {
-    if (threadIdx.x == 0) s_slot = atomicAdd(b.f.counter + 1, 1);
+    if (threadIdx.x == 0)
+      s_slot = (b.f.err && *b.f.err != 0) ? b.f.n_pairs : atomicAdd(b.f.counter + 1, 1);
     __syncthreads();
     const long long slot = s_slot;
     __syncthreads();
     if (slot >= b.f.n_pairs) break;
     const PairDesc pd = b.f.desc[slot];
-    pair_backward<TC>(b, pd, ws, gs, cs);
+    if (!pair_backward<TC>(b, pd, ws, gs, cs, sc, phase)) {
+      if (threadIdx.x == 0) {
+        b.f.status[pd.pair] = 3;
+        atomicExch(b.f.err, 1);
+      }
+      break;
+    }
     __syncthreads();
   }
 }

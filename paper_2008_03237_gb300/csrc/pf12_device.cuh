@@ -12,7 +12,7 @@
 
 namespace pf12 {
 
-struct __align__(16) GemmSmem {
+struct __align__(128) GemmSmem {
   double buf[2 * kBK * (kTile + 1)];  // A and B tiles (as double or as float)
 };
 
@@ -339,27 +339,131 @@ __device__ __forceinline__ void solve_right_lowerT(const double* L, int64_t ld, 
 // ---------------------------------------------------------------------------
 // Gather mode: sieve pair P's four factor blocks out of the per-orbital
 // pair-extended blocks (Sec. "F12 integral transformations") into dst as
-// packed p x m blocks [Ag_i, Ag_j, Af_i, Af_j].  Rows go to warps, columns to
-// lanes: the column indices are runs of whole atoms, so reads are coalesced.
-__device__ __forceinline__ void sieve_pair(const FwdParams& prm, const PairDesc& pd, double* dst) {
+// packed p x m blocks [Ag_i, Ag_j, Af_i, Af_j].
+//
+// TMA path (tensor maps present): the pair's rows go in groups of four through
+// tile::gather4 loads (4 arbitrary rows x 128 columns, column start rounded
+// down to 16 bytes) into shared memory, up to 8 loads per mbarrier phase; the
+// threads then pick the pair's columns out of each staged window.  Plain path
+// (no maps, or columns spread over more than 32 windows): rows to warps,
+// columns to lanes (the columns are atom runs, so reads are coalesced).
+struct SieveCtl {
+  unsigned long long mbar;  // TMA completion barrier
+  int win[33];              // window start indices into the pair's column map
+  int flag;                 // bounded wait expired
+};
+
+constexpr int kSieveW = 128;         // columns per gather4 box
+constexpr int kSieveOps = 8;         // gather4 loads per phase (8 x 4 KB staging)
+constexpr uint32_t kSieveWait = 1u << 26;
+
+__device__ __forceinline__ void sieve_init(SieveCtl& sc) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(&sc.mbar))
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sc.flag = 0;
+  }
+  __syncthreads();
+}
+
+// Returns false (uniformly) when a bounded TMA wait expired.
+__device__ __forceinline__ bool sieve_pair(const FwdParams& prm, const PairDesc& pd, double* dst,
+                                           GemmSmem& gs, SieveCtl& sc, uint32_t& phase) {
+  static_assert(sizeof(GemmSmem) >= kSieveOps * 4 * kSieveW * sizeof(double), "sieve staging");
   const GatherDesc g = prm.gdesc[pd.pair];
   const int p = pd.p, m = pd.m;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int32_t* rows[2] = {prm.map_pao + g.map_pao, prm.map_pao + g.map_pao + p};
   const int32_t* cols[2] = {prm.map_aux + g.map_aux, prm.map_aux + g.map_aux + m};
   const int64_t off[2] = {g.off_i, g.off_j};
   const int32_t ldo[2] = {g.ld_i, g.ld_j};
+  const int orb[2] = {g.orb_i, g.orb_j};
+  double* tiles = gs.buf;   // kSieveOps x 4 x kSieveW doubles, 128-byte aligned
+  const uint32_t tiles_s = (uint32_t)__cvta_generic_to_shared(tiles);
+  const uint32_t mbar_s = (uint32_t)__cvta_generic_to_shared(&sc.mbar);
 #pragma unroll 1
   for (int x = 0; x < 4; ++x) {
     const int side = x & 1;
-    const double* src = (x < 2 ? prm.Bg : prm.Bf) + off[side];
+    const int32_t* rw = rows[side];
+    const int32_t* cl = cols[side];
     double* out = dst + (int64_t)x * p * m;
-    for (int r = warp; r < p; r += kThreads / 32) {
-      const double* row = src + (int64_t)rows[side][r] * ldo[side];
-      for (int c = lane; c < m; c += 32) out[(int64_t)r * m + c] = row[cols[side][c]];
+    const int c_lo = cl[0] & ~1;
+    const int nw = (cl[m - 1] - c_lo) / kSieveW + 1;
+    if (!prm.tmaps || nw > 32) {
+      const double* src = (x < 2 ? prm.Bg : prm.Bf) + off[side];
+      for (int r = warp; r < p; r += kThreads / 32) {
+        const double* row = src + (int64_t)rw[r] * ldo[side];
+        for (int c = lane; c < m; c += 32) out[(int64_t)r * m + c] = row[cl[c]];
+      }
+      __syncthreads();
+      continue;
+    }
+    const char* tmap = static_cast<const char*>(prm.tmaps) + (size_t)(2 * orb[side] + (x >= 2)) * 128;
+    // window w holds pair columns [win[w], win[w + 1])
+    if (tid <= nw) {
+      const int bound = c_lo + tid * kSieveW;
+      int lo = 0, hi = m;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cl[mid] < bound) lo = mid + 1; else hi = mid;
+      }
+      sc.win[tid] = lo;
+    }
+    __syncthreads();
+    const int ngroups = (p + 3) / 4;
+    const int total = ngroups * nw;
+    for (int op0 = 0; op0 < total; op0 += kSieveOps) {
+      const int nops = min(kSieveOps, total - op0);
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_s),
+                     "r"((uint32_t)(nops * 4 * kSieveW * 8))
+                     : "memory");
+        for (int q = 0; q < nops; ++q) {
+          const int op = op0 + q, grp = op / nw, w = op - grp * nw;
+          int r[4];
+#pragma unroll
+          for (int s4 = 0; s4 < 4; ++s4) r[s4] = rw[min(4 * grp + s4, p - 1)];
+          const int xc = c_lo + w * kSieveW;
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+              " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(tiles_s + q * 4 * kSieveW * 8),
+              "l"(tmap), "r"(xc), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(mbar_s)
+              : "memory");
+        }
+        uint32_t done = 0;
+        for (uint32_t it = 0; it < kSieveWait && !done; ++it)
+          asm volatile(
+              "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+              " selp.u32 %0, 1, 0, p;\n}\n"
+              : "=r"(done)
+              : "r"(mbar_s), "r"(phase)
+              : "memory");
+        if (!done) sc.flag = 1;
+      }
+      __syncthreads();
+      phase ^= 1u;
+      if (sc.flag) return false;
+      // pick the pair's columns out of the staged windows
+      for (int q = 0; q < nops; ++q) {
+        const int op = op0 + q, grp = op / nw, w = op - grp * nw;
+        const int ca = sc.win[w], cb = sc.win[w + 1];
+        const int xc = c_lo + w * kSieveW;
+        const double* tq = tiles + q * 4 * kSieveW;
+        const int width = cb - ca;
+        for (int e = tid; e < 4 * width; e += kThreads) {
+          const int s4 = e / width, c = ca + (e - s4 * width);
+          const int r = 4 * grp + s4;
+          if (r < p) out[(int64_t)r * m + c] = tq[s4 * kSieveW + (cl[c] - xc)];
+        }
+      }
+      __syncthreads();
     }
   }
-  __syncthreads();
+  return true;
 }
 
 // ---------------------------------------------------------------------------

@@ -22,8 +22,9 @@ namespace pf12 {
 //   F = [At^f_i ; At^f_j]         (2k x ld)        ->  [At^f_i - Ct_i J_f ; At^f_j]
 //   V = (At^f_i - Ct_i J_f) Ct_j^T + Ct_i At^f_j^T
 template <typename TC>
-__device__ void pair_forward(const FwdParams& prm, const PairDesc& pd, double* ws, GemmSmem& gs,
-                             CholSmem& cs, double (*red)[kThreads / 32]) {
+__device__ bool pair_forward(const FwdParams& prm, const PairDesc& pd, double* ws, GemmSmem& gs,
+                             CholSmem& cs, double (*red)[kThreads / 32], SieveCtl& sc,
+                             uint32_t& phase) {
   const int tid = threadIdx.x;
   const int p = pd.p, k = pd.k, m = pd.m;
   const int64_t ld = (m + 3) / 4 * 4;
@@ -44,7 +45,7 @@ __device__ void pair_forward(const FwdParams& prm, const PairDesc& pd, double* w
                            prm.Afj + pd.off_pm};
   if (prm.gdesc) {
     double* G = ws + fwd_sieve_off(k, m);
-    sieve_pair(prm, pd, G);
+    if (!sieve_pair(prm, pd, G, gs, sc, phase)) return false;
     for (int x = 0; x < 4; ++x) Asrc[x] = G + (int64_t)x * p * m;
   }
   // S1': At^x = Q^T A^x  (k x m), A(a, mu) = Q[mu * k + a]
@@ -65,7 +66,7 @@ __device__ void pair_forward(const FwdParams& prm, const PairDesc& pd, double* w
       prm.dx[2 * (int64_t)pd.pair] = nan;
       prm.dx[2 * (int64_t)pd.pair + 1] = nan;
     }
-    return;
+    return true;
   }
   double* Ci = M + (int64_t)m * ld;
   double* Cj = M + (int64_t)(m + k) * ld;
@@ -106,6 +107,7 @@ __device__ void pair_forward(const FwdParams& prm, const PairDesc& pd, double* w
     prm.dx[2 * P + 1] = sx;
     prm.status[P] = (isfinite(sd) && isfinite(sx)) ? 0 : 2;
   }
+  return true;
 }
 
 template <typename TC, int MINB>
@@ -114,15 +116,24 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_forward_kernel(FwdParams 
   __shared__ CholSmem cs;
   __shared__ double red[2][kThreads / 32];
   __shared__ long long s_slot;
+  __shared__ SieveCtl sc;
+  uint32_t phase = 0;
+  if (prm.gdesc) sieve_init(sc);
   double* ws = prm.work + (int64_t)blockIdx.x * prm.ws_stride;
   for (;;) {
-    if (threadIdx.x == 0) s_slot = atomicAdd(prm.counter, 1);
+    if (threadIdx.x == 0) s_slot = (prm.err && *prm.err != 0) ? prm.n_pairs : atomicAdd(prm.counter, 1);
     __syncthreads();
     const long long slot = s_slot;
     __syncthreads();
     if (slot >= prm.n_pairs) break;
     const PairDesc pd = prm.desc[slot];
-    pair_forward<TC>(prm, pd, ws, gs, cs, red);
+    if (!pair_forward<TC>(prm, pd, ws, gs, cs, red, sc, phase)) {
+      if (threadIdx.x == 0) {
+        prm.status[pd.pair] = 3;
+        atomicExch(prm.err, 1);
+      }
+      break;
+    }
     __syncthreads();
   }
 }
@@ -134,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_forward_kernel(FwdParams 
 // expired (the pair gets status 3 and the kernel stops taking pairs).
 __device__ bool pair_forward_tc(const FwdParams& prm, const PairDesc& pd, double* ws, GemmSmem& gs,
                                 CholSmem& cs, double (*red)[kThreads / 32], tc::Stage& st,
-                                tc::Ctrl& ctrl, int* s_flag) {
+                                tc::Ctrl& ctrl, int* s_flag, SieveCtl& sc, uint32_t& phase) {
   const int tid = threadIdx.x;
   const int p = pd.p, k = pd.k, m = pd.m;
   const int64_t ld = (m + 3) / 4 * 4;
@@ -150,7 +161,7 @@ __device__ bool pair_forward_tc(const FwdParams& prm, const PairDesc& pd, double
                            prm.Afj + pd.off_pm};
   if (prm.gdesc) {
     double* G = ws + fwd_sieve_off(k, m);
-    sieve_pair(prm, pd, G);
+    if (!sieve_pair(prm, pd, G, gs, sc, phase)) return false;
     for (int x = 0; x < 4; ++x) Asrc[x] = G + (int64_t)x * p * m;
   }
   double* Adst[4] = {M + (int64_t)m * ld, M + (int64_t)(m + k) * ld, F, F + (int64_t)k * ld};
@@ -224,6 +235,9 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_forward_tc_kernel(FwdPara
   double (*red)[kThreads / 32] = reinterpret_cast<double (*)[kThreads / 32]>(tail + sizeof(tc::Ctrl));
   long long* s_slot = reinterpret_cast<long long*>(tail + sizeof(tc::Ctrl) + 2 * (kThreads / 32) * sizeof(double));
   int* s_flag = reinterpret_cast<int*>(s_slot + 1);
+  __shared__ SieveCtl sc;
+  uint32_t phase = 0;
+  if (prm.gdesc) sieve_init(sc);
   if (threadIdx.x == 0) *s_flag = 0;
   tc::setup(ctrl);
   double* ws = prm.work + (int64_t)blockIdx.x * prm.ws_stride;
@@ -234,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_forward_tc_kernel(FwdPara
     __syncthreads();
     if (slot >= prm.n_pairs) break;
     const PairDesc pd = prm.desc[slot];
-    if (!pair_forward_tc(prm, pd, ws, gs, cs, red, st, ctrl, s_flag)) {
+    if (!pair_forward_tc(prm, pd, ws, gs, cs, red, st, ctrl, s_flag, sc, phase)) {
       if (threadIdx.x == 0) {
         prm.status[pd.pair] = 3;
         atomicExch(prm.err, 1);

@@ -25,6 +25,7 @@ struct GatherDesc {
   int64_t off_i, off_j;      // element offsets of orbital i's and j's blocks
   int64_t map_pao, map_aux;  // offsets of the pair's 2p row / 2m column indices
   int32_t ld_i, ld_j;        // row strides of those blocks
+  int32_t orb_i, orb_j;      // orbital indices (tensor-map lookup)
 };
 
 struct FwdParams {
@@ -43,6 +44,9 @@ struct FwdParams {
   const GatherDesc* gdesc;   // indexed by the caller's pair index
   const double *Bg, *Bf;     // per-orbital extended blocks (Coulomb, F12)
   const int32_t *map_pao, *map_aux;
+  // TMA tensor maps of the orbital blocks ([2o] Bg, [2o + 1] Bf, 128 bytes each,
+  // box 128 columns x 1 row) or null: the sieve then uses plain loads
+  const void* tmaps;
 };
 
 struct BwdParams {

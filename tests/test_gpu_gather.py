@@ -26,7 +26,7 @@ def _gather_workload(n_domo=6, n_somo=1, cutoff=3):
     return G.make_gather(base)
 
 
-def _upload_gather(gw, precision, variant=None):
+def _upload_gather(gw, precision, variant=None, sieve_plain=False):
     import paper_2008_03237_gb300 as pf
     wl = gw.base
     blocks, (P, M, ld, off, tot) = G.orbital_blocks(gw)
@@ -34,7 +34,7 @@ def _upload_gather(gw, precision, variant=None):
     host, lay = S.packed_inputs(wl)   # J, Q, T of the pair sizes (A's unused)
     dev = {n: torch.from_numpy(host[n]).cuda() for n in ("Jg", "Jf", "Q", "T")}
     bl = {n: torch.from_numpy(v).cuda() for n, v in blocks.items()}
-    eng = pf.PairF12(precision, variant=variant)
+    eng = pf.PairF12(precision, variant=variant, sieve_plain=sieve_plain)
     eng.upload_pairs_gather(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, bl,
                             dict(off_orb=off, ext_pao=P, ext_aux=M, ext_ld=ld),
                             dict(map_pao=mp, map_aux=ma, off_map_pao=op, off_map_aux=oa), dev, lay)
@@ -58,13 +58,16 @@ def _packed_from_gather(gw):
     return buf, lay
 
 
+@pytest.mark.parametrize("sieve_plain", [False, True])
 @pytest.mark.parametrize("precision,variant", [("fp64", 0), ("fp64", 1), ("mixed_fp32", 1),
                                                ("mixed_fp32", 2)])
-def test_gather_equals_packed_and_oracle(built, precision, variant):
+def test_gather_equals_packed_and_oracle(built, precision, variant, sieve_plain):
+    """TMA tile::gather4 sieve and plain-load sieve alike."""
     gw = _gather_workload()
     wl = gw.base
-    eng, *_ = _upload_gather(gw, precision, variant)
+    eng, *_ = _upload_gather(gw, precision, variant, sieve_plain)
     eng.fit()
+    assert eng.stats()["sieve_tma"] == (0 if sieve_plain else 1)
     E, e = eng.energy()
     e = e.cpu().numpy()
     from gpu_helpers import upload_host
@@ -76,10 +79,11 @@ def test_gather_equals_packed_and_oracle(built, precision, variant):
     assert np.abs(e - ref["e_pair"]).max() <= tol
 
 
-def test_gather_backward_scatters_in_pair_order(built):
+@pytest.mark.parametrize("sieve_plain", [False, True])
+def test_gather_backward_scatters_in_pair_order(built, sieve_plain):
     gw = _gather_workload(5, 2, 4)
     wl = gw.base
-    eng, bl, (P, M, ld, off, tot), lay = _upload_gather(gw, "fp64")
+    eng, bl, (P, M, ld, off, tot), lay = _upload_gather(gw, "fp64", sieve_plain=sieve_plain)
     eng.fit()
     eng.energy()
     outs = []
