@@ -85,6 +85,10 @@ typedef struct {
                               pf12_stats_t.tile_config); unavailable ones are refused */
   int sieve_plain;         /* gather mode: 1 = sieve with plain loads; 0 = TMA tile::gather4
                               loads when every orbital block starts and strides on 16 bytes */
+  int debug_wait_timeout;  /* tests only, keep 0: the tensor-core and TMA paths issue no work
+                              before their first barrier wait and poll it briefly, so the
+                              bounded wait expires; the pair gets status 3 and pf12_energy
+                              returns PF12_ERR_TIMEOUT with the context still usable */
 } pf12_opts;
 
 /* Packed ("plain mode") per-pair tensors.  Pair P's blocks start at element

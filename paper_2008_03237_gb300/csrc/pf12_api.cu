@@ -75,6 +75,7 @@ struct pf12_ctx {
   size_t cap_tmaps = 0;
   bool use_tma = false;
   bool sieve_plain = false;        // option: sieve with plain loads only
+  uint32_t debug_wait_polls = 0;   // test hook (pf12_opts.debug_wait_timeout)
 
   // graph of the forward launch
   cudaGraph_t graph = nullptr;
@@ -176,6 +177,7 @@ pf12::FwdParams fwd_params(pf12_ctx* c) {
   f.ws_stride = c->ws_stride;
   f.counter = c->d_counter;
   f.err = c->d_counter + 2;
+  f.debug_wait_polls = c->debug_wait_polls;
   if (c->gather) {
     f.tmaps = c->use_tma ? c->d_tmaps : nullptr;
     f.gdesc = c->d_gdesc;
@@ -210,6 +212,7 @@ int pf12_create(pf12_ctx** out, const pf12_opts* o) {
     }
     c->forced = o->force_variant;
     c->sieve_plain = o->sieve_plain != 0;
+    c->debug_wait_polls = o->debug_wait_timeout ? 4096u : 0u;
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -422,7 +422,7 @@ __device__ __forceinline__ bool sieve_pair(const FwdParams& prm, const PairDesc&
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_s),
                      "r"((uint32_t)(nops * 4 * kSieveW * 8))
                      : "memory");
-        for (int q = 0; q < nops; ++q) {
+        for (int q = 0; q < nops && prm.debug_wait_polls == 0; ++q) {
           const int op = op0 + q, grp = op / nw, w = op - grp * nw;
           int r[4];
 #pragma unroll
@@ -435,7 +435,8 @@ __device__ __forceinline__ bool sieve_pair(const FwdParams& prm, const PairDesc&
               : "memory");
         }
         uint32_t done = 0;
-        for (uint32_t it = 0; it < kSieveWait && !done; ++it)
+        const uint32_t limit = prm.debug_wait_polls ? prm.debug_wait_polls : kSieveWait;
+        for (uint32_t it = 0; it < limit && !done; ++it)
           asm volatile(
               "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
               " selp.u32 %0, 1, 0, p;\n}\n"

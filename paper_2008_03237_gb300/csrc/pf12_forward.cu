@@ -167,7 +167,8 @@ __device__ bool pair_forward_tc(const FwdParams& prm, const PairDesc& pd, double
   double* Adst[4] = {M + (int64_t)m * ld, M + (int64_t)(m + k) * ld, F, F + (int64_t)k * ld};
 #pragma unroll 1
   for (int x = 0; x < 4; ++x)
-    if (!tc::gemm<true, true>(m, k, p, Asrc[x], m, Q, k, Adst[x], ld, 1.0, false, st, ctrl, s_flag))
+    if (!tc::gemm<true, true>(m, k, p, Asrc[x], m, Q, k, Adst[x], ld, 1.0, false, st, ctrl, s_flag,
+                              prm.debug_wait_polls))
       return false;
   __syncthreads();
   const bool ok = chol_augmented(M, ld, m, m + 2 * k, cs, gs);

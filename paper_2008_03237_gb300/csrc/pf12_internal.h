@@ -47,6 +47,9 @@ struct FwdParams {
   // TMA tensor maps of the orbital blocks ([2o] Bg, [2o + 1] Bf, 128 bytes each,
   // box 128 columns x 1 row) or null: the sieve then uses plain loads
   const void* tmaps;
+  // test hook: nonzero = issue no tensor-core / TMA work before the first
+  // barrier wait and give that wait this many polls, so it expires
+  uint32_t debug_wait_polls;
 };
 
 struct BwdParams {

@@ -122,9 +122,9 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t adesc, uint64_t bd
       : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(Ctrl& c) {
+__device__ __forceinline__ bool mbar_wait(Ctrl& c, uint32_t limit = kWaitLimit) {
   const uint32_t addr = smem_addr(&c.mbar), par = c.phase;
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -141,10 +141,13 @@ __device__ __forceinline__ bool mbar_wait(Ctrl& c) {
 // for r < min(128, M - r0), n < min(128, N - n0).  accumulate = false
 // overwrites Out.  Called by all threads; returns false (uniformly) on a
 // barrier timeout.
+// debug_polls != 0 (tests only): issue no MMA, so nothing arrives on the
+// barrier, and poll it debug_polls times: the bounded wait expires.
 template <bool TA, bool TB>
 __device__ bool gemm_tile(int M, int N, int K, const double* A, int64_t lda, const double* B,
                           int64_t ldb, double* Out, int64_t ldo, int r0, int n0, double alpha,
-                          bool accumulate, Stage& st, Ctrl& c, int* s_flag) {
+                          bool accumulate, Stage& st, Ctrl& c, int* s_flag,
+                          uint32_t debug_polls = 0) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nthreads = blockDim.x;
   const int rows = min(kM, M - r0);
@@ -188,7 +191,7 @@ __device__ bool gemm_tile(int M, int N, int K, const double* A, int64_t lda, con
     fence_before();
     __syncthreads();
     fence_after();
-    if (tid == 0) {
+    if (tid == 0 && debug_polls == 0) {
       const uint32_t d = c.tmem_base;
       const uint32_t ah = smem_addr(st.a_hi), al = smem_addr(st.a_lo);
       const uint32_t bh = smem_addr(st.b_hi), bl = smem_addr(st.b_lo);
@@ -209,7 +212,7 @@ __device__ bool gemm_tile(int M, int N, int K, const double* A, int64_t lda, con
     }
     // one thread polls the barrier; the others park on the CTA barrier, so
     // the co-resident CTAs' FP64 work keeps the issue slots
-    if (tid == 0 && !mbar_wait(c)) *s_flag = 1;
+    if (tid == 0 && !mbar_wait(c, debug_polls ? debug_polls : kWaitLimit)) *s_flag = 1;
     __syncthreads();
     if (tid == 0) c.phase ^= 1u;   // read again only after the next staging barrier
     if (*s_flag) return false;
@@ -259,11 +262,11 @@ __device__ bool gemm_tile(int M, int N, int K, const double* A, int64_t lda, con
 template <bool TA, bool TB>
 __device__ bool gemm(int M, int N, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
                      double* Out, int64_t ldo, double alpha, bool accumulate, Stage& st, Ctrl& c,
-                     int* s_flag) {
+                     int* s_flag, uint32_t debug_polls = 0) {
   for (int n0 = 0; n0 < N; n0 += kNmax)
     for (int r0 = 0; r0 < M; r0 += kM)
       if (!gemm_tile<TA, TB>(M, N, K, A, lda, B, ldb, Out, ldo, r0, n0, alpha, accumulate, st, c,
-                             s_flag))
+                             s_flag, debug_polls))
         return false;
   __syncthreads();
   return true;

@@ -212,3 +212,24 @@ def test_autograd_function_and_finite_differences(built):
             an = float((g * d).sum())
             noise = 8 * 2.2e-16 * E0 / h
             assert abs(fd - an) <= 1e-7 * abs(an) + noise, (n, fd, an)
+
+
+def test_bounded_wait_expiry_is_reported_and_context_survives(built):
+    """Failure detection without a fault: with the test hook the tensor-core
+    path issues no MMA, so its completion barrier never flips; the bounded
+    wait expires, the pair is flagged (status 3), pf12_energy returns TIMEOUT,
+    and the same process then runs a normal evaluation correctly."""
+    import paper_2008_03237_gb300 as pf
+    wl = _mini()
+    t, lay = upload_host(wl)
+    eng = pf.PairF12("mixed_fp32", variant=2, debug_wait_timeout=True)
+    eng.upload_pairs(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
+    eng.fit()
+    with pytest.raises(pf.Pf12Error) as ei:
+        eng.energy()
+    assert ei.value.code == -5
+    assert (eng.pair_status() == 3).any()
+    eng.close()
+    ref = O.run(wl)
+    r = run(wl, "mixed_fp32", t=t, lay=lay, want_V=False, variant=2)
+    assert np.abs(r["e_pair"] - ref["e_pair"]).max() <= 1e-5 * np.abs(ref["e_pair"]).max()
