@@ -175,74 +175,94 @@ __device__ __forceinline__ void cta_gemm(int M, int N, int K, const double* A, i
 }
 
 // ---------------------------------------------------------------------------
-// Right-looking blocked Cholesky of the leading m x m block of M (row-major,
-// leading dimension ld, lower triangle used), FP64, extended to the extra rows
+// Blocked Cholesky of the leading m x m block of M (row-major, leading
+// dimension ld, lower triangle used), FP64, extended to the extra rows
 // [m, rows): on return M[0:m, 0:m] holds L (lower) and M[m:rows, 0:m] holds
 // M[m:rows] L^{-T}, i.e. the forward solve rides along the factorisation as
-// extra rows of every panel solve and trailing update.  Entries above the
-// diagonal are scratch.  Returns false on every thread when a pivot is not
-// positive and finite (J_g not SPD).
+// extra rows of every panel solve and update.  Entries above the diagonal are
+// scratch.  Returns false on every thread when a pivot is not positive and
+// finite (J_g not SPD).
+//
+// Panels are kNB = 32 wide and grouped kLook at a time: inside a group each
+// panel is first brought up to date by the group's earlier panels (a narrow
+// left-looking update), then factored (warp-level diagonal block, in-register
+// panel solve); the columns right of the group get one update of depth
+// kLook * 32.  The trailing matrix is thus read and written once per group
+// instead of once per panel; the flop count is unchanged.
+constexpr int kLook = 4;
+
 __device__ __forceinline__ bool chol_augmented(double* M, int64_t ld, int m, int rows,
                                                CholSmem& cs, GemmSmem& gs) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int kb = 0; kb < m; kb += kNB) {
-    const int nb = min(kNB, m - kb);
-    for (int e = tid; e < nb * nb; e += kThreads) {
-      const int r = e / nb, c = e - r * nb;
-      cs.d[r][c] = (c <= r) ? M[(int64_t)(kb + r) * ld + kb + c] : 0.0;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      int ok = 1;
-      for (int j = 0; j < nb; ++j) {
-        const double djj = cs.d[j][j];
-        if (!(djj > 0.0) || !isfinite(djj)) ok = 0;
-        const double l = sqrt(djj);
-        const double inv = 1.0 / l;
-        __syncwarp();
-        if (lane == j) { cs.d[j][j] = l; cs.inv[j] = inv; }
-        if (lane > j && lane < nb) cs.d[lane][j] *= inv;
-        __syncwarp();
-        if (lane > j && lane < nb) {
-          const double lrj = cs.d[lane][j];
-          for (int c = j + 1; c <= lane; ++c) cs.d[lane][c] = fma(-lrj, cs.d[c][j], cs.d[lane][c]);
-        }
-        __syncwarp();
+  for (int g0 = 0; g0 < m; g0 += kLook * kNB) {
+    const int gend = min(m, g0 + kLook * kNB);
+    for (int kb = g0; kb < gend; kb += kNB) {
+      const int nb = min(kNB, m - kb);
+      // bring panel [kb, kb + nb) up to date with the group's earlier panels
+      if (kb > g0) {
+        for (int R = kb; R < rows; R += kTile)
+          cta_gemm_tile<double, false, true>(rows, kb + nb, kb - g0, M + g0, ld, M + g0, ld, M, ld,
+                                             R, kb, -1.0, true, gs, m);
+        __syncthreads();
       }
-      if (lane == 0) cs.ok = ok;
-    }
-    __syncthreads();
-    if (!cs.ok) return false;
-    for (int e = tid; e < nb * nb; e += kThreads) {
-      const int r = e / nb, c = e - r * nb;
-      if (c <= r) M[(int64_t)(kb + r) * ld + kb + c] = cs.d[r][c];
-    }
-    // panel solve: rows below the diagonal block, X L_kk^T = A_panel
-    for (int r = kb + nb + tid; r < rows; r += kThreads) {
-      double* row = M + (int64_t)r * ld + kb;
-      double x[kNB];
-#pragma unroll
-      for (int t = 0; t < kNB; ++t) x[t] = (t < nb) ? row[t] : 0.0;
-#pragma unroll
-      for (int t = 0; t < kNB; ++t) {
-        if (t < nb) {
-          double s = x[t];
-#pragma unroll
-          for (int q = 0; q < t; ++q) s = fma(-x[q], cs.d[t][q], s);
-          x[t] = s * cs.inv[t];
-        }
+      for (int e = tid; e < nb * nb; e += kThreads) {
+        const int r = e / nb, c = e - r * nb;
+        cs.d[r][c] = (c <= r) ? M[(int64_t)(kb + r) * ld + kb + c] : 0.0;
       }
+      __syncthreads();
+      if (warp == 0) {
+        int ok = 1;
+        for (int j = 0; j < nb; ++j) {
+          const double djj = cs.d[j][j];
+          if (!(djj > 0.0) || !isfinite(djj)) ok = 0;
+          const double l = sqrt(djj);
+          const double inv = 1.0 / l;
+          __syncwarp();
+          if (lane == j) { cs.d[j][j] = l; cs.inv[j] = inv; }
+          if (lane > j && lane < nb) cs.d[lane][j] *= inv;
+          __syncwarp();
+          if (lane > j && lane < nb) {
+            const double lrj = cs.d[lane][j];
+            for (int c = j + 1; c <= lane; ++c) cs.d[lane][c] = fma(-lrj, cs.d[c][j], cs.d[lane][c]);
+          }
+          __syncwarp();
+        }
+        if (lane == 0) cs.ok = ok;
+      }
+      __syncthreads();
+      if (!cs.ok) return false;
+      for (int e = tid; e < nb * nb; e += kThreads) {
+        const int r = e / nb, c = e - r * nb;
+        if (c <= r) M[(int64_t)(kb + r) * ld + kb + c] = cs.d[r][c];
+      }
+      // panel solve: rows below the diagonal block, X L_kk^T = A_panel
+      for (int r = kb + nb + tid; r < rows; r += kThreads) {
+        double* row = M + (int64_t)r * ld + kb;
+        double x[kNB];
 #pragma unroll
-      for (int t = 0; t < kNB; ++t)
-        if (t < nb) row[t] = x[t];
+        for (int t = 0; t < kNB; ++t) x[t] = (t < nb) ? row[t] : 0.0;
+#pragma unroll
+        for (int t = 0; t < kNB; ++t) {
+          if (t < nb) {
+            double s = x[t];
+#pragma unroll
+            for (int q = 0; q < t; ++q) s = fma(-x[q], cs.d[t][q], s);
+            x[t] = s * cs.inv[t];
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < kNB; ++t)
+          if (t < nb) row[t] = x[t];
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    // trailing update of the lower part (and of every extra row)
-    const int rb = kb + nb;
+    // one deep update of everything right of the group (lower part and every
+    // extra row) with the group's kLook panels
+    const int rb = gend;
     for (int R = rb; R < rows; R += kTile)
       for (int C = rb; C < m && C < R + kTile; C += kTile)
-        cta_gemm_tile<double, false, true>(rows, m, nb, M + kb, ld, M + kb, ld, M, ld, R, C, -1.0,
-                                           true, gs, m);
+        cta_gemm_tile<double, false, true>(rows, m, gend - g0, M + g0, ld, M + g0, ld, M, ld, R, C,
+                                           -1.0, true, gs, m);
     __syncthreads();
   }
   return true;
