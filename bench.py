@@ -35,6 +35,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "F12 pairs/s & TFLOP/s, mixed-prec vs plain FP64 on 1 GB300 at ≤1 µEh error"
 FP64_PEAK_TFLOPS = 1.25     # nominal GB300 dense FP64 (DFMA), 152 SMs x 4 flop/clk x 2.07 GHz
+
+
+def measured_peaks():
+    """The generated MEASURED_PEAKS.json (BF16 tensor TFLOP/s, HBM GB/s), if present."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
 CHEM_SCALE_PER_ORB = 4.8e-3  # Eh per orbital (C160H322 F12 correction / valence orbitals)
 
 
@@ -443,7 +453,11 @@ def main():
                    "m_range": [int(wl.n_aux.min()), int(wl.n_aux.max())],
                    "l2": f"inputs {byts / 1e9:.0f} GB >> 129 MB L2, no flush"},
         "tflops": {"fp64": f64 / ms / 1e9, "mixed_part": fmix / ms / 1e9,
-                   "total": (f64 + fmix) / ms / 1e9},
+                   "total": (f64 + fmix) / ms / 1e9,
+                   "fp64_frac_of_peak": f64 / ms / 1e9 / FP64_PEAK_TFLOPS,
+                   "mixed_part_frac_of_bf16_tensor_peak":
+                       (fmix / ms / 1e9 / measured_peaks()["bf16_tflops"])
+                       if measured_peaks().get("bf16_tflops") else None},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": traffic_bytes(args, wl, byts, o["stats"]["tile_config"]),
@@ -476,6 +490,9 @@ def main():
         rate, cores, sample = cpu_oracle_rate(wl, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
+        rate1, _, sample1 = cpu_oracle_rate(wl, max(3.0, args.cpu_seconds / 3), threads=1)
+        line["cpu_baseline_1thread"] = {"value": rate1, "unit": "pairs/s", "cores": 1,
+                                        "kind": "oracle", "sample": sample1}
     print(json.dumps(line), flush=True)
 
 

@@ -56,3 +56,21 @@ def gather_pair_energies(e_local, shard, n_pairs, group=None):
     for P in range(n_pairs):
         total += full[P, 0] + full[P, 1] + full[P, 2]
     return full, total
+
+
+def reduce_orbital_gradients(blocks, group=None):
+    """Sum every rank's per-orbital gradient blocks (gather-mode adjoint: each
+    rank scatter-adds the pairs of its shard) and return the total on every
+    rank.  The ranks' contributions are added in rank order after an
+    all-gather, so the result is the same on every rank and reproducible for a
+    given world size and partition."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    local = torch.as_tensor(np.ascontiguousarray(blocks, dtype=np.float64))
+    parts = [torch.zeros_like(local) for _ in range(world)]
+    dist.all_gather(parts, local, group=group)
+    total = parts[0].clone()
+    for r in range(1, world):
+        total += parts[r]
+    return total.numpy()
