@@ -168,44 +168,88 @@ class ClockSampler:
 # --------------------------------------------------------------------------- CPU oracle
 
 
-def cpu_oracle_rate(wl, budget_s, threads=None):
-    """FP64 CPU oracle (as it stands) on a deterministic sample of wl's pairs:
-    inputs drawn first, only the oracle's evaluation timed.  Runs in a child
-    process with an explicit BLAS thread count.  Returns (pairs/s, threads, sample)."""
-    threads = threads or os.cpu_count() or 1
-    env = dict(os.environ, OPENBLAS_NUM_THREADS=str(threads), OMP_NUM_THREADS=str(threads),
-               MKL_NUM_THREADS=str(threads))
-    code = f"""
-import sys, time, json
-sys.path.insert(0, {ROOT!r})
+_ORACLE_WORKER = """
+import sys, os, time, json
+sys.path.insert(0, {root!r})
 import numpy as np
 import oracle, synthetic as S
 from bench import make_workload
-wl = make_workload({wl.meta.get('bench_name', 'c160h321')!r}, {int(wl.meta.get('bench_max', 0))})
-n = wl.n_pairs
-order = np.random.default_rng(12345).permutation(n)
-done, t_used, pairs = 0, 0.0, []
-cache = {{}}
-for P in order:
-    P = int(P)
-    cache[P] = S.pair_inputs(wl, P)
-    t0 = time.perf_counter()
-    oracle.run(wl, pairs=[P], inputs=lambda q: cache[q])
-    t_used += time.perf_counter() - t0
-    del cache[P]
-    done += 1
-    pairs.append(P)
-    if t_used >= {budget_s}:
-        break
-print(json.dumps(dict(rate=done / t_used, done=done, seconds=t_used)))
+wl = make_workload({name!r}, {max_pairs})
+rank, nproc, budget, n_pairs, steps, go = {rank}, {nproc}, {budget}, {n_pairs}, {steps}, {go!r}
+order = np.random.default_rng(12345).permutation(wl.n_pairs)[rank::nproc][:n_pairs]
+cache = [(int(P), S.pair_inputs(wl, int(P))) for P in order]   # drawn before any timing
+open(go + ".ready%d" % rank, "w").close()
+res = []
+for s in range(steps):
+    while not os.path.exists(go + ".%d" % s):
+        time.sleep(0.01)
+    done, t_used = 0, 0.0
+    for P, t in cache:
+        t0 = time.perf_counter()
+        oracle.run(wl, pairs=[P], inputs=lambda q: t)
+        t_used += time.perf_counter() - t0
+        done += 1
+        if t_used >= budget:
+            break
+    res.append((done, t_used))
+    open(go + ".done%d.%d" % (s, rank), "w").close()
+print(json.dumps(res))
 """
-    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
-                       cwd=ROOT)
-    if r.returncode != 0:
-        raise RuntimeError("cpu oracle failed: " + r.stderr[-2000:])
-    out = json.loads(r.stdout.strip().splitlines()[-1])
-    return out["rate"], threads, (f"{out['done']} pairs of {wl.name} drawn by a fixed permutation "
-                                  f"(seed 12345), {out['seconds']:.1f} s of oracle time")
+
+
+def cpu_oracle_rate(wl, budget_s, threads=None, steps=1):
+    """FP64 CPU oracle (as it stands) on a deterministic sample of wl's pairs,
+    parallel over pairs: `threads` worker processes with one BLAS thread each
+    (default: every host core).  Each worker draws the inputs of its share of
+    the sample once, before any timing; then, `steps` times, all workers are
+    released together and each evaluates its pairs in order until its oracle
+    time reaches budget_s.  A step's rate is all pairs evaluated in it / the
+    slowest worker's oracle time.  Returns (per-step pairs/s list, workers,
+    sample description)."""
+    import shutil
+    import tempfile
+    nproc = threads or os.cpu_count() or 1
+    # pairs each worker draws: the oracle runs tens of pairs/s per core on the
+    # bench workload, drawing the inputs about ten times slower
+    n_pairs = 12 + int(6 * budget_s)
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    tmp = tempfile.mkdtemp(prefix="pf12_oracle_")
+    go = os.path.join(tmp, "go")
+    procs = []
+    for r in range(nproc):
+        code = _ORACLE_WORKER.format(root=ROOT, name=wl.meta.get("bench_name", "c160h321"),
+                                     max_pairs=int(wl.meta.get("bench_max", 0)), rank=r,
+                                     nproc=nproc, budget=float(budget_s), n_pairs=n_pairs,
+                                     steps=int(steps), go=go)
+        procs.append(subprocess.Popen([sys.executable, "-c", code], env=env, cwd=ROOT,
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+
+    def wait_files(names):
+        while not all(os.path.exists(x) for x in names):
+            if any(p.poll() not in (None, 0) for p in procs):
+                _, err = next(p for p in procs if p.poll() not in (None, 0)).communicate()
+                raise RuntimeError("cpu oracle worker failed: " + err[-2000:])
+            time.sleep(0.02)
+    wait_files([go + ".ready%d" % r for r in range(nproc)])
+    for s in range(steps):       # one step at a time: all workers start together
+        open(go + ".%d" % s, "w").close()
+        wait_files([go + ".done%d.%d" % (s, r) for r in range(nproc)])
+    per = []
+    for p in procs:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("cpu oracle worker failed: " + err[-2000:])
+        per.append(json.loads(out.strip().splitlines()[-1]))
+    shutil.rmtree(tmp, ignore_errors=True)
+    rates, done_last, slow_last = [], 0, 0.0
+    for s in range(steps):
+        done = sum(w[s][0] for w in per)
+        slowest = max(w[s][1] for w in per)
+        rates.append(done / slowest)
+        done_last, slow_last = done, slowest
+    return rates, nproc, (f"{done_last} pairs of {wl.name} per step (fixed permutation, seed "
+                          f"12345; inputs drawn before timing) over {nproc} worker process(es) x "
+                          f"1 BLAS thread, {slow_last:.1f} s of oracle time in the slowest worker")
 
 
 # --------------------------------------------------------------------------- our arm
@@ -487,10 +531,10 @@ def main():
     if "e2e" not in line:
         line["e2e"] = None
     if not args.no_cpu and world == 1:
-        rate, cores, sample = cpu_oracle_rate(wl, args.cpu_seconds)
+        (rate,), cores, sample = cpu_oracle_rate(wl, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
-        rate1, _, sample1 = cpu_oracle_rate(wl, max(3.0, args.cpu_seconds / 3), threads=1)
+        (rate1,), _, sample1 = cpu_oracle_rate(wl, max(3.0, args.cpu_seconds / 3), threads=1)
         line["cpu_baseline_1thread"] = {"value": rate1, "unit": "pairs/s", "cores": 1,
                                         "kind": "oracle", "sample": sample1}
     print(json.dumps(line), flush=True)
@@ -560,13 +604,10 @@ def run_reference(args, rank, world):
     wl = make_workload(args.workload, args.max_pairs)
     wl.meta["bench_name"] = args.workload
     wl.meta["bench_max"] = args.max_pairs
+    # the sample's inputs are drawn once; every step times the oracle on it
     budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    rates = []
-    for i in range(args.warmup + args.steps):
-        rate, cores, sample = cpu_oracle_rate(wl, budget)
-        if i >= args.warmup:
-            rates.append(rate)
-    value = float(np.mean(rates))
+    rates, cores, sample = cpu_oracle_rate(wl, budget, steps=args.warmup + args.steps)
+    value = float(np.mean(rates[args.warmup:]))
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
