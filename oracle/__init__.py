@@ -6,4 +6,6 @@ synthetic/ generator alone.
 """
 from .pairf12 import (DOMO, SOMO, local_fit, robust_kernel, pno_transform,
                       amplitude_contractions, spin_multiplicities, pair_energies,
-                      pair_forward, energy_weights, pair_gradient, run, kahan_total)
+                      pair_forward, energy_weights, pair_gradient, run, kahan_total,
+                      augment_pno, virtual_spaces, opposite_spin_orientations,
+                      spin_case_weights, spin_case_energies)

@@ -23,6 +23,14 @@ primitives and no blocking, fusion or reordering:
          e_ab = n_ab (3 d + x) / 8,  e_aa = n_aa (d - x) / 4,  e_bb = n_bb (d - x) / 4
   6. E = sum over pairs, FP64, in pair-list order.
 
+With SOMO augmentation (Sec. "SOMO handling"), every PAO domain also holds
+the n_s SOMOs and the PAO-to-PNO matrix is extended by an n_s x n_s identity:
+Q_aug = blockdiag(Q, I).  The factors then have p + n_s rows and V, T are
+(k + n_s) x (k + n_s).  A SOMO is alpha-occupied and beta-unoccupied, so the
+alpha virtual space of a pair is its PNOs and the beta virtual space its PNOs
+and the SOMOs; each spin case sums only over its own virtual pairs
+(spin_case_energies).
+
 Readings of the paper that these steps fix (the paper gives the spin-orbital
 equations only): the direct and exchange amplitude terms of one pair are
 Vt_dir = d / 2 and Vt_exch = x / 2 (the factor 1/2 of Eq. Vtilde), the
@@ -90,19 +98,94 @@ def pair_energies(d, x, mult):
             n_bb * (d - x) / 4.0)
 
 
+# ---------------------------------------------------------------- SOMO augmentation
+
+
+def augment_pno(Q, n_s):
+    """Sec. "SOMO handling": the PAO-to-PNO matrix extended by an n_s x n_s
+    identity for the SOMOs that every PAO domain holds: blockdiag(Q, I)."""
+    p, k = Q.shape
+    Qa = np.zeros((p + n_s, k + n_s))
+    Qa[:p, :k] = Q
+    Qa[p:, k:] = np.eye(n_s)
+    return Qa
+
+
+def virtual_spaces(k, n_s):
+    """Boolean masks over the k + n_s virtuals of an augmented pair: alpha
+    virtuals are the PNOs (the SOMOs are alpha-occupied), beta virtuals are the
+    PNOs and the SOMOs (beta-unoccupied)."""
+    va = np.zeros(k + n_s, bool)
+    va[:k] = True
+    vb = np.ones(k + n_s, bool)
+    return va, vb
+
+
+def opposite_spin_orientations(kind_i, kind_j, same_orbital):
+    """(c1, c2): whether the opposite-spin pair (i alpha, j beta) and the pair
+    (j alpha, i beta) are occupied spin-orbital pairs; c1 + c2 = n_ab."""
+    c1 = 1 if kind_j == DOMO else 0
+    c2 = 1 if (kind_i == DOMO and not same_orbital) else 0
+    return c1, c2
+
+
+def spin_case_weights(kind_i, kind_j, same_orbital, va, vb):
+    """Weight matrices Wd, Wx with E_P = sum_ab Wd_ab V_ab T_ab + Wx_ab V_ab T_ba.
+
+    Spin case by spin case (alpha electron of the opposite-spin pair first):
+      (i alpha, j beta):  3/8 sum_{a in va, b in vb} V_ab T_ab + 1/8 sum_{a in vb, b in va} V_ab T_ba
+      (j alpha, i beta):  the same with V, T transposed (electron 1 on j)
+      same spin sigma:    1/4 sum_{a, b in v_sigma} V_ab (T_ab - T_ba)
+    which with va = vb = all virtuals is n_ab (3d + x)/8 + (n_aa + n_bb)(d - x)/4."""
+    c1, c2 = opposite_spin_orientations(kind_i, kind_j, same_orbital)
+    _, n_aa, n_bb = spin_multiplicities(kind_i, kind_j, same_orbital)
+    ab = np.outer(va, vb).astype(float)
+    ba = np.outer(vb, va).astype(float)
+    aa = np.outer(va, va).astype(float)
+    bb = np.outer(vb, vb).astype(float)
+    Wd = 3.0 / 8.0 * (c1 * ab + c2 * ba) + (n_aa * aa + n_bb * bb) / 4.0
+    Wx = 1.0 / 8.0 * (c1 * ba + c2 * ab) - (n_aa * aa + n_bb * bb) / 4.0
+    return Wd, Wx
+
+
+def spin_case_energies(V, T, kind_i, kind_j, same_orbital, va, vb):
+    """(e_ab, e_aa, e_bb) with each spin case restricted to its own virtuals."""
+    c1, c2 = opposite_spin_orientations(kind_i, kind_j, same_orbital)
+    _, n_aa, n_bb = spin_multiplicities(kind_i, kind_j, same_orbital)
+
+    def opposite(Vo, To):
+        return (3.0 / 8.0 * float(np.sum((Vo * To)[np.ix_(va, vb)]))
+                + 1.0 / 8.0 * float(np.sum((Vo * To.T)[np.ix_(vb, va)])))
+
+    def same(v):
+        blk = np.ix_(v, v)
+        return 0.25 * float(np.sum((V * T)[blk]) - np.sum((V * T.T)[blk]))
+    return (c1 * opposite(V, T) + c2 * opposite(V.T, T.T), n_aa * same(va), n_bb * same(vb))
+
+
 # ---------------------------------------------------------------- per pair
 
 
-def pair_forward(t, kind_i, kind_j, same_orbital):
-    """All intermediates of one pair (t: dict of the pair's input tensors)."""
+def pair_forward(t, kind_i, kind_j, same_orbital, n_somo_aug=0):
+    """All intermediates of one pair (t: dict of the pair's input tensors).
+
+    n_somo_aug > 0: SOMO-augmented pair; t's factors have p + n_somo_aug rows
+    (the SOMOs last), Q is p x k and T is (k + n_somo_aug) square."""
     C_i, C_j = local_fit(t["Agi"], t["Agj"], t["Jg"])
     K = robust_kernel(t["Afi"], t["Afj"], C_i, C_j, t["Jf"])
-    V = pno_transform(K, t["Q"])
+    Q = augment_pno(t["Q"], n_somo_aug) if n_somo_aug else t["Q"]
+    V = pno_transform(K, Q)
     d, x = amplitude_contractions(V, t["T"])
     mult = spin_multiplicities(kind_i, kind_j, same_orbital)
-    e = pair_energies(d, x, mult)
-    return {"C_i": C_i, "C_j": C_j, "K": K, "V": V, "d": d, "x": x,
-            "mult": mult, "e": e}
+    out = {"C_i": C_i, "C_j": C_j, "K": K, "V": V, "d": d, "x": x, "mult": mult}
+    if n_somo_aug:
+        va, vb = virtual_spaces(t["Q"].shape[1], n_somo_aug)
+        out["e"] = spin_case_energies(V, t["T"], kind_i, kind_j, same_orbital, va, vb)
+        out["W"] = spin_case_weights(kind_i, kind_j, same_orbital, va, vb)
+        out["Q_aug"] = Q
+    else:
+        out["e"] = pair_energies(d, x, mult)
+    return out
 
 
 def energy_weights(mult):
@@ -122,13 +205,22 @@ def pair_gradient(t, fwd, dE=1.0):
         dC_i = Gb (A^f_j - C_j J_f),   dC_j = Gb^T (A^f_i - C_i J_f)
         dA^g_x = dC_x J_g^{-1}
     """
-    alpha, beta = energy_weights(fwd["mult"])
-    T, V, K, Q = t["T"], fwd["V"], fwd["K"], t["Q"]
+    T, V, K = t["T"], fwd["V"], fwd["K"]
     C_i, C_j = fwd["C_i"], fwd["C_j"]
-    G_V = dE * (alpha * T + beta * T.T)
-    g = {"T": dE * (alpha * V + beta * V.T)}
+    if "W" in fwd:     # SOMO-augmented: per-element weights, Q_aug = blockdiag(Q, I)
+        Wd, Wx = fwd["W"]
+        Q = fwd["Q_aug"]
+        G_V = dE * (Wd * T + Wx * T.T)
+        g = {"T": dE * (Wd * V + (Wx * V).T)}
+    else:
+        alpha, beta = energy_weights(fwd["mult"])
+        Q = t["Q"]
+        G_V = dE * (alpha * T + beta * T.T)
+        g = {"T": dE * (alpha * V + beta * V.T)}
     Gb = Q @ G_V @ Q.T
-    g["Q"] = K @ Q @ G_V.T + K.T @ Q @ G_V
+    # only the PNO block of Q_aug is an input (the identity block is fixed)
+    p, k = t["Q"].shape
+    g["Q"] = (K @ Q @ G_V.T + K.T @ Q @ G_V)[:p, :k]
     g["Afi"] = Gb @ C_j
     g["Afj"] = Gb.T @ C_i
     dC_i = Gb @ (t["Afj"] - C_j @ t["Jf"])
@@ -159,7 +251,8 @@ def run(wl, pairs=None, inputs=None, want_V=False, want_grad=False, dE=1.0):
     for n, P in enumerate(idx):
         t = get(P)
         i, j = int(wl.pi[P]), int(wl.pj[P])
-        f = pair_forward(t, int(wl.orb_kind[i]), int(wl.orb_kind[j]), i == j)
+        f = pair_forward(t, int(wl.orb_kind[i]), int(wl.orb_kind[j]), i == j,
+                         int(getattr(wl, "somo_aug", 0)))
         e_pair[n] = f["e"]
         dd[n], xx[n] = f["d"], f["x"]
         if want_V:

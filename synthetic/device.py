@@ -81,7 +81,7 @@ def fill(wl, t, lay, scratch_bytes=1 << 30):
     for name, tid in tids.items():
         meta = np.zeros(n, META)
         meta["off"] = lay["off_pm"]
-        meta["rows"] = wl.n_pao
+        meta["rows"] = wl.n_rows
         meta["cols"] = wl.n_aux
         meta["key"] = keys
         tt = np.full(n, tid, np.int32)

@@ -68,6 +68,7 @@ class Workload:
     decay: np.ndarray         # float64 per pair, s_P scaling all four DF factors
     metric_shift: float = METRIC_SHIFT
     meta: dict = field(default_factory=dict)
+    somo_aug: int = 0         # SOMO-augmented PNO space: SOMO rows / virtuals per pair
 
     @property
     def n_orb(self):
@@ -83,10 +84,29 @@ class Workload:
         w = Workload(name or self.name + "[sub]", self.seed, self.n_domo, self.n_somo,
                      self.orb_kind, self.pi[idx], self.pj[idx], self.n_pao[idx],
                      self.n_pno[idx], self.n_aux[idx], self.decay[idx],
-                     self.metric_shift, dict(self.meta))
+                     self.metric_shift, dict(self.meta), self.somo_aug)
         base = self.meta.get("pair_key", np.arange(self.n_pairs, dtype=np.int64))
         w.meta["pair_key"] = np.asarray(base)[idx]
         return w
+
+    def augmented(self):
+        """The same pair list in the SOMO-augmented PNO space (Sec. "SOMO
+        handling"): every pair's factors gain the n_somo SOMO rows (drawn as
+        rows p .. p + n_s - 1 of the same Philox stream, so rows 0 .. p - 1 are
+        unchanged) and its amplitudes become (k + n_s) square."""
+        return Workload(self.name + "[somo-aug]", self.seed, self.n_domo, self.n_somo,
+                        self.orb_kind, self.pi, self.pj, self.n_pao, self.n_pno, self.n_aux,
+                        self.decay, self.metric_shift, dict(self.meta), int(self.n_somo))
+
+    @property
+    def n_rows(self):
+        """Rows of each pair's factor blocks: p, plus the SOMOs when augmented."""
+        return self.n_pao.astype(np.int64) + self.somo_aug
+
+    @property
+    def n_virt(self):
+        """Virtual dimension of V and T per pair: k, plus the SOMOs when augmented."""
+        return self.n_pno.astype(np.int64) + self.somo_aug
 
     def pair_key(self, P):
         """Philox counter word that identifies pair P (its index in the full list)."""
@@ -282,9 +302,10 @@ def metric_from_int(Z, m, shift):
 
 def pair_inputs(wl, P):
     """Host tensors of pair P: dict Agi, Agj, Afi, Afj (p x m), Jg, Jf (m x m),
-    Q (p x k), T (k x k), all float64 row-major."""
+    Q (p x k), T (k x k), all float64 row-major.  Augmented workloads: the
+    factors are (p + n_s) x m and T is (k + n_s) square."""
     key = wl.pair_key(P)
-    p, k, m = int(wl.n_pao[P]), int(wl.n_pno[P]), int(wl.n_aux[P])
+    p, k, m = int(wl.n_rows[P]), int(wl.n_pno[P]), int(wl.n_aux[P])
     diag = int(wl.pi[P]) == int(wl.pj[P])
     c = factor_scale(wl.decay[P])
     out = {}
@@ -316,7 +337,7 @@ def pno_coefficients(wl, P):
 def amplitudes(wl, P):
     """k x k amplitudes, std 1e-2; symmetrised for diagonal pairs (t^{ab}_{ii} = t^{ba}_{ii})."""
     key = wl.pair_key(P)
-    k = int(wl.n_pno[P])
+    k = int(wl.n_virt[P])
     T = _gauss16(wl.seed, key, TID_T, k * k, amplitude_scale()).reshape(k, k)
     if int(wl.pi[P]) == int(wl.pj[P]):
         T = (T + T.T) * 0.5
@@ -340,8 +361,9 @@ def packed_offsets(wl):
     p = wl.n_pao.astype(np.int64)
     k = wl.n_pno.astype(np.int64)
     m = wl.n_aux.astype(np.int64)
+    r, v = wl.n_rows, wl.n_virt       # factor rows and virtual dimension (augmented)
     out = {}
-    for name, sz in (("pm", p * m), ("mm", m * m), ("pk", p * k), ("kk", k * k)):
+    for name, sz in (("pm", r * m), ("mm", m * m), ("pk", p * k), ("kk", v * v)):
         padded = _round_up(sz)
         off = np.zeros(len(sz), np.int64)
         if len(sz) > 1:

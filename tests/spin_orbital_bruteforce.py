@@ -36,8 +36,22 @@ def gauss_jordan_inverse(A):
     return M[:, n:]
 
 
-def spatial_pair_intermediate(t):
-    """V_ab = <ab|O|ij> for one pair from its inputs, by explicit index contractions."""
+def spatial_pair_intermediate(t, n_somo=0):
+    """V_ab = <ab|O|ij> for one pair from its inputs, by explicit index contractions.
+
+    n_somo > 0: the factors carry the SOMO rows last and the virtual space is
+    the PNOs followed by the SOMOs themselves (Sec. "SOMO handling"), i.e. the
+    transformation sends PAO row u < p through Q and SOMO row p + s to virtual
+    k + s unchanged."""
+    if n_somo:
+        p, k = t["Q"].shape
+        Q = np.zeros((p + n_somo, k + n_somo))
+        for u in range(p):
+            for a in range(k):
+                Q[u, a] = t["Q"][u, a]
+        for q in range(n_somo):
+            Q[p + q, k + q] = 1.0
+        t = dict(t, Q=Q)
     Jinv = gauss_jordan_inverse(t["Jg"])
     C_i = np.einsum("uX,XY->uY", t["Agi"], Jinv)
     C_j = np.einsum("uX,XY->uY", t["Agj"], Jinv)
@@ -62,13 +76,18 @@ def spin_projector_weights():
     return 0.5 * P0 + 0.25 * P1
 
 
-def _spin_orbital_pair_energy(Vs, Ts, sP, sR, W):
+def _spin_orbital_pair_energy(Vs, Ts, sP, sR, W, n_alpha_virt=None):
     """2 Vt^{PR}_{PR} for electron 1 in spin sP, electron 2 in spin sR, given the
-    spatial V^{oP oR} (Vs) and T^{oP oR} (Ts) of the ordered orbital pair."""
+    spatial V^{oP oR} (Vs) and T^{oP oR} (Ts) of the ordered orbital pair.
+
+    The virtual spin orbitals are (a, beta) for every spatial virtual a and
+    (a, alpha) for a < n_alpha_virt only (default: all): in the SOMO-augmented
+    space the trailing virtuals are SOMOs, which are alpha-occupied."""
     k = Vs.shape[0]
-    n = 2 * k
-    spin = np.array([ALPHA] * k + [BETA] * k)
-    orb = np.array(list(range(k)) * 2)
+    na = k if n_alpha_virt is None else n_alpha_virt
+    spin = np.array([ALPHA] * na + [BETA] * k)
+    orb = np.array(list(range(na)) + list(range(k)))
+    n = len(orb)
     O = np.zeros((n, n))
     t = np.zeros((n, n))
     for A in range(n):
@@ -83,10 +102,11 @@ def _spin_orbital_pair_energy(Vs, Ts, sP, sR, W):
     return 2.0 * Vt
 
 
-def bruteforce_pair_energies(wl, V_of_pair, T_of_pair):
+def bruteforce_pair_energies(wl, V_of_pair, T_of_pair, n_alpha_virt_of_pair=None):
     """Per pair of the list, the (alpha-beta, alpha-alpha, beta-beta) sums of
     2 Vt^{PR}_{PR} over all occupied spin-orbital pairs P < R on that pair's
-    two orbitals."""
+    two orbitals.  n_alpha_virt_of_pair(P), when given, limits the alpha
+    virtual spin orbitals of pair P to its leading spatial virtuals."""
     W = spin_projector_weights()
     occ = [(o, ALPHA) for o in range(wl.n_orb)]
     occ += [(o, BETA) for o in range(wl.n_orb) if int(wl.orb_kind[o]) == 0]
@@ -102,7 +122,8 @@ def bruteforce_pair_energies(wl, V_of_pair, T_of_pair):
             V, T = V_of_pair(P), T_of_pair(P)
             if oP > oR:                      # electron 1 sits on the pair's j orbital
                 V, T = V.T, T.T
-            val = _spin_orbital_pair_energy(V, T, sP, sR, W)
+            na = None if n_alpha_virt_of_pair is None else n_alpha_virt_of_pair(P)
+            val = _spin_orbital_pair_energy(V, T, sP, sR, W, na)
             case = 0 if sP != sR else (1 if sP == ALPHA else 2)
             e[P, case] += val
     return e
