@@ -65,6 +65,8 @@ def parse():
                     help="pair-streamed run: inputs drawn on the device batch by batch "
                          "(workloads larger than HBM); 0 = inputs resident")
     ap.add_argument("--backward", action="store_true", help="streamed run: adjoint per batch too")
+    ap.add_argument("--augment-somo", action="store_true",
+                    help="SOMO-augmented PNO space (no e2e or CPU legs)")
     ap.add_argument("--variant", type=int, default=None,
                     help="force a forward kernel variant instead of autotuning (profiling)")
     return ap.parse_args()
@@ -93,16 +95,21 @@ def traffic_bytes(args, wl, byts, variant):
     the same kernel variant scaled by algorithmic bytes; None when the timed
     kernel is not the captured one."""
     cap = TRAFFIC_CAPTURE
-    if variant != cap["variant"] or args.precision != cap["precision"] or args.stream_gb:
+    if (variant != cap["variant"] or args.precision != cap["precision"] or args.stream_gb
+            or args.augment_somo):
         return None
     return cap["bytes"] * byts / cap["alg_bytes"]
 
 
 def flops_bytes(wl):
+    """Algorithmic FP64 flops, mixable flops and input bytes of one forward
+    pass.  SOMO-augmented lists: the solves and V act on k + n_s virtuals, the
+    factors have p + n_s rows, Q stays p x k."""
     p, k, m = (wl.n_pao.astype(float), wl.n_pno.astype(float), wl.n_aux.astype(float))
-    f64 = float((m ** 3 / 3 + 4 * k * m * m).sum())
-    fmix = float((8 * p * k * m + 2 * k * m * m + 4 * k * k * m).sum())
-    byts = float((8 * (4 * p * m + 2 * m * m + p * k + k * k)).sum())
+    v, r = wl.n_virt.astype(float), wl.n_rows.astype(float)
+    f64 = float((m ** 3 / 3 + 4 * v * m * m).sum())
+    fmix = float((8 * p * k * m + 2 * v * m * m + 4 * v * v * m).sum())
+    byts = float((8 * (4 * r * m + 2 * m * m + p * k + v * v)).sum())
     return f64, fmix, byts
 
 
@@ -272,13 +279,16 @@ def run_ours(args, rank, world, local_rank):
     wl = make_workload(args.workload, args.max_pairs, rank)
     wl.meta["bench_name"] = args.workload
     wl.meta["bench_max"] = args.max_pairs
+    if args.augment_somo:
+        wl = wl.augmented()
+        args.no_e2e = args.no_cpu = True
     f64, fmix, byts = flops_bytes(wl)
     t, lay = device.allocate(wl)
     device.fill(wl, t, lay)
 
     def make(prec):
         var = args.variant if (args.variant is not None and (prec != "fp64" or args.variant < 2)) else None
-        eng = pf.PairF12(prec, variant=var)
+        eng = pf.PairF12(prec, variant=var, augment_somo=args.augment_somo)
         eng.upload_pairs(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
         return eng
 
@@ -491,7 +501,8 @@ def main():
         "vs_baseline": None, "dtype": "f64+f32" if args.precision != "fp64" else "f64",
         "data": "synthetic (seeded Philox4x32-10 draws, device-resident)",
         "config": {"workload": wl.name, "pairs": n_pairs, "orbitals": wl.n_orb,
-                   "somos": wl.n_somo, "precision": args.precision,
+                   "somos": wl.n_somo, "somo_augmented": bool(wl.somo_aug),
+                   "precision": args.precision,
                    "p_range": [int(wl.n_pao.min()), int(wl.n_pao.max())],
                    "k_range": [int(wl.n_pno.min()), int(wl.n_pno.max())],
                    "m_range": [int(wl.n_aux.min()), int(wl.n_aux.max())],

@@ -89,6 +89,14 @@ typedef struct {
                               before their first barrier wait and poll it briefly, so the
                               bounded wait expires; the pair gets status 3 and pf12_energy
                               returns PF12_ERR_TIMEOUT with the context still usable */
+  int augment_somo;        /* 1: SOMO-augmented PNO space (Sec. "SOMO handling"): every PAO
+                              domain holds the n_s SOMOs of orb_kind and the PAO-to-PNO matrix
+                              is blockdiag(Q, I_{n_s}).  Per pair, Ag/Af blocks are
+                              (p + n_s) x m (SOMO rows last), Q stays p x k, T and V are
+                              (k + n_s) x (k + n_s) (SOMO virtuals last).  Alpha virtuals are
+                              the PNOs, beta virtuals the PNOs and SOMOs, and each spin case
+                              sums over its own virtuals.  Packed mode only (gather mode:
+                              PF12_ERR_UNSUPPORTED); k + n_s <= 256.  0: plain PNO space */
 } pf12_opts;
 
 /* Packed ("plain mode") per-pair tensors.  Pair P's blocks start at element

@@ -56,14 +56,17 @@ class PairF12:
     energy sums in both."""
 
     def __init__(self, precision="fp64", workspace_bytes=0, stream=None, tuner_cache=None,
-                 variant=None, sieve_plain=False, debug_wait_timeout=False):
+                 variant=None, sieve_plain=False, debug_wait_timeout=False, augment_somo=False):
         """variant: None = autotune, else 0 / 1 (SIMT, 2 / 3 CTAs per SM) or
-        2 (tcgen05 tensor-core contractions, mixed precision only)."""
+        2 (tcgen05 tensor-core contractions, mixed precision only).
+        augment_somo: SOMO-augmented PNO space (factor blocks (p + n_s) x m with
+        the SOMO rows last, Q p x k, T and V (k + n_s) square)."""
         self._L = lib()
         self._cache = tuner_cache.encode() if tuner_cache else None
         opts = _lib.Opts(_lib.PRECISION[precision], None, int(workspace_bytes), 1, self._cache,
                          -1 if variant is None else int(variant), int(bool(sieve_plain)),
-                         int(bool(debug_wait_timeout)))
+                         int(bool(debug_wait_timeout)), int(bool(augment_somo)))
+        self.augment_somo = bool(augment_somo)
         h = ctypes.c_void_p()
         self._check(self._L.pf12_create(ctypes.byref(h), ctypes.byref(opts)), None)
         self._h = h

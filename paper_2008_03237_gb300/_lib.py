@@ -20,7 +20,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("deterministic", ctypes.c_int),
                 ("tuner_cache", ctypes.c_char_p), ("force_variant", ctypes.c_int),
-                ("sieve_plain", ctypes.c_int), ("debug_wait_timeout", ctypes.c_int)]
+                ("sieve_plain", ctypes.c_int), ("debug_wait_timeout", ctypes.c_int),
+                ("augment_somo", ctypes.c_int)]
 
 
 class Tensors(ctypes.Structure):

@@ -8,6 +8,9 @@
 //   dQ    = Af_i H1^T + Af_j H2^T + Ag_i H3^T + Ag_j H4^T                 (p x k)
 // which is the chain rule of V = Q^T K Q, K = A^f_i C_j^T + C_i A^f_j^T -
 // C_i J_f C_j^T, C = A^g J_g^{-1} with J_g, J_f symmetric and held constant.
+// SOMO-augmented pairs (Sec. "SOMO handling") use Q_aug = blockdiag(Q, I): the
+// SOMO rows of dA are the SOMO rows of H, dQ takes the PNO rows of H only, and
+// alpha, beta become per-block weights (alpha virtuals exclude the SOMOs).
 #include <cuda_runtime.h>
 
 #include "pf12_device.cuh"
@@ -47,10 +50,19 @@ __device__ bool pair_backward(const BwdParams& b, const PairDesc& pd, double* ws
 
   for (int r = tid >> 5; r < m; r += kThreads / 32)
     for (int c = tid & 31; c < m; c += 32) M[(int64_t)r * ld + c] = Jg[(int64_t)r * m + c];
-  cta_gemm<TC, true, false>(k, m, p, Q, k, Agi, m, M + (int64_t)m * ld, ld, 1.0, false, gs);
-  cta_gemm<TC, true, false>(k, m, p, Q, k, Agj, m, M + (int64_t)(m + k) * ld, ld, 1.0, false, gs);
-  cta_gemm<TC, true, false>(k, m, p, Q, k, Afi, m, F, ld, 1.0, false, gs);
-  cta_gemm<TC, true, false>(k, m, p, Q, k, Afj, m, F + (int64_t)k * ld, ld, 1.0, false, gs);
+  // SOMO-augmented pair: Q_aug = blockdiag(Q, I), Q is p x kq
+  const int s = pd.s, kq = k - s;
+  cta_gemm<TC, true, false>(kq, m, p, Q, kq, Agi, m, M + (int64_t)m * ld, ld, 1.0, false, gs);
+  cta_gemm<TC, true, false>(kq, m, p, Q, kq, Agj, m, M + (int64_t)(m + k) * ld, ld, 1.0, false, gs);
+  cta_gemm<TC, true, false>(kq, m, p, Q, kq, Afi, m, F, ld, 1.0, false, gs);
+  cta_gemm<TC, true, false>(kq, m, p, Q, kq, Afj, m, F + (int64_t)k * ld, ld, 1.0, false, gs);
+  if (s) {
+    copy_somo_rows(Agi, p, s, m, M + (int64_t)m * ld, ld, kq);
+    copy_somo_rows(Agj, p, s, m, M + (int64_t)(m + k) * ld, ld, kq);
+    copy_somo_rows(Afi, p, s, m, F, ld, kq);
+    copy_somo_rows(Afj, p, s, m, F + (int64_t)k * ld, ld, kq);
+    __syncthreads();
+  }
 
   if (!chol_augmented(M, ld, m, m + 2 * k, cs, gs)) {
     if (tid == 0) prm.status[pd.pair] = 1;
@@ -77,10 +89,21 @@ __device__ bool pair_backward(const BwdParams& b, const PairDesc& pd, double* ws
   const double alpha = 3.0 * pd.n_ab / 8.0 + (pd.n_aa + pd.n_bb) / 4.0;
   const double beta = pd.n_ab / 8.0 - (pd.n_aa + pd.n_bb) / 4.0;
   double* dT = b.dT ? b.dT + pd.off_kk : nullptr;
-  for (int e = tid; e < k * k; e += kThreads) {
-    const int a = e / k, c = e - a * k;
-    GV[a * ldk + c] = b.dE * (alpha * T[a * k + c] + beta * T[c * k + a]);
-    if (dT) dT[e] = b.dE * (alpha * Vl[a * ldk + c] + beta * Vl[c * ldk + a]);
+  if (s == 0) {
+    for (int e = tid; e < k * k; e += kThreads) {
+      const int a = e / k, c = e - a * k;
+      GV[a * ldk + c] = b.dE * (alpha * T[a * k + c] + beta * T[c * k + a]);
+      if (dT) dT[e] = b.dE * (alpha * Vl[a * ldk + c] + beta * Vl[c * ldk + a]);
+    }
+  } else {   // augmented: weights by virtual block (PNO / SOMO of a and of c)
+    for (int e = tid; e < k * k; e += kThreads) {
+      const int a = e / k, c = e - a * k;
+      double wd, wx, wd_t, wx_t;
+      somo_block_weights(pd, 2 * (a >= kq) + (c >= kq), wd, wx);
+      somo_block_weights(pd, 2 * (c >= kq) + (a >= kq), wd_t, wx_t);
+      GV[a * ldk + c] = b.dE * (wd * T[a * k + c] + wx * T[c * k + a]);
+      if (dT) dT[e] = b.dE * (wd * Vl[a * ldk + c] + wx_t * Vl[c * ldk + a]);
+    }
   }
   __syncthreads();
 
@@ -96,21 +119,31 @@ __device__ bool pair_backward(const BwdParams& b, const PairDesc& pd, double* ws
   // H1 = G_V Ct_j, H2 = G_V^T Ct_i
   cta_gemm<TC, false, false>(k, m, k, GV, ldk, Cj, ld, H1, ld, 1.0, false, gs);
   cta_gemm<TC, true, false>(k, m, k, GV, ldk, Ci, ld, H2, ld, 1.0, false, gs);
-  if (b.dAfi) cta_gemm<TC, false, false>(p, m, k, Q, k, H1, ld, b.dAfi + pd.off_pm, m, 1.0, false, gs);
-  if (b.dAfj) cta_gemm<TC, false, false>(p, m, k, Q, k, H2, ld, b.dAfj + pd.off_pm, m, 1.0, false, gs);
-  if (dQ) {
-    cta_gemm<TC, false, true>(p, k, m, Afi, m, H1, ld, dQ, k, 1.0, false, gs);
-    cta_gemm<TC, false, true>(p, k, m, Afj, m, H2, ld, dQ, k, 1.0, true, gs);
+  if (b.dAfi) cta_gemm<TC, false, false>(p, m, kq, Q, kq, H1, ld, b.dAfi + pd.off_pm, m, 1.0, false, gs);
+  if (b.dAfj) cta_gemm<TC, false, false>(p, m, kq, Q, kq, H2, ld, b.dAfj + pd.off_pm, m, 1.0, false, gs);
+  if (s) {
+    if (b.dAfi) copy_somo_grad_rows(H1, ld, kq, s, m, b.dAfi + pd.off_pm, p);
+    if (b.dAfj) copy_somo_grad_rows(H2, ld, kq, s, m, b.dAfj + pd.off_pm, p);
   }
+  if (dQ) {
+    cta_gemm<TC, false, true>(p, kq, m, Afi, m, H1, ld, dQ, kq, 1.0, false, gs);
+    cta_gemm<TC, false, true>(p, kq, m, Afj, m, H2, ld, dQ, kq, 1.0, true, gs);
+  }
+  if (s) __syncthreads();   // H1, H2 are overwritten next
   // H3 = G_V Z_j^T, H4 = G_V^T Z_i^T
   cta_gemm<TC, false, false>(k, m, k, GV, ldk, Zj, ld, H1, ld, 1.0, false, gs);
   cta_gemm<TC, true, false>(k, m, k, GV, ldk, Zi, ld, H2, ld, 1.0, false, gs);
-  if (b.dAgi) cta_gemm<TC, false, false>(p, m, k, Q, k, H1, ld, b.dAgi + pd.off_pm, m, 1.0, false, gs);
-  if (b.dAgj) cta_gemm<TC, false, false>(p, m, k, Q, k, H2, ld, b.dAgj + pd.off_pm, m, 1.0, false, gs);
-  if (dQ) {
-    cta_gemm<TC, false, true>(p, k, m, Agi, m, H1, ld, dQ, k, 1.0, true, gs);
-    cta_gemm<TC, false, true>(p, k, m, Agj, m, H2, ld, dQ, k, 1.0, true, gs);
+  if (b.dAgi) cta_gemm<TC, false, false>(p, m, kq, Q, kq, H1, ld, b.dAgi + pd.off_pm, m, 1.0, false, gs);
+  if (b.dAgj) cta_gemm<TC, false, false>(p, m, kq, Q, kq, H2, ld, b.dAgj + pd.off_pm, m, 1.0, false, gs);
+  if (s) {
+    if (b.dAgi) copy_somo_grad_rows(H1, ld, kq, s, m, b.dAgi + pd.off_pm, p);
+    if (b.dAgj) copy_somo_grad_rows(H2, ld, kq, s, m, b.dAgj + pd.off_pm, p);
   }
+  if (dQ) {
+    cta_gemm<TC, false, true>(p, kq, m, Agi, m, H1, ld, dQ, kq, 1.0, true, gs);
+    cta_gemm<TC, false, true>(p, kq, m, Agj, m, H2, ld, dQ, kq, 1.0, true, gs);
+  }
+  if (s) __syncthreads();
   if (tid == 0) prm.status[pd.pair] = 0;
   return true;
 }

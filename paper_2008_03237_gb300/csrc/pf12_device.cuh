@@ -506,4 +506,83 @@ __device__ __forceinline__ void cta_sum2(double& a, double& b, double (*red)[kTh
   b = sb;
 }
 
+// ---------------------------------------------------------------------------
+// SOMO-augmented PNO space (Sec. "SOMO handling"): every PAO domain holds the
+// s SOMOs and the PAO-to-PNO matrix is blockdiag(Q, I_s).  A pair's factor
+// blocks carry the SOMO rows after its p PAO rows; its virtual space is the
+// kq = k - s PNOs followed by the SOMOs.  The SOMOs are alpha-occupied, so the
+// alpha virtuals are the PNOs only and the beta virtuals are all k.
+
+// Rows kq .. k - 1 of At^x = Q_aug^T A^x: the SOMO rows p .. p + s - 1 of A^x
+// (the identity block of Q_aug), copied exactly.
+__device__ __forceinline__ void copy_somo_rows(const double* A, int p, int s, int m, double* At,
+                                               int64_t ld, int kq) {
+  for (int r = threadIdx.x >> 5; r < s; r += kThreads / 32)
+    for (int c = threadIdx.x & 31; c < m; c += 32)
+      At[(int64_t)(kq + r) * ld + c] = A[(int64_t)(p + r) * m + c];
+}
+
+// Rows p .. p + s - 1 of dA^x = Q_aug H: the SOMO rows kq .. k - 1 of H.
+__device__ __forceinline__ void copy_somo_grad_rows(const double* H, int64_t ld, int kq, int s,
+                                                    int m, double* dA, int p) {
+  for (int r = threadIdx.x >> 5; r < s; r += kThreads / 32)
+    for (int c = threadIdx.x & 31; c < m; c += 32)
+      dA[(int64_t)(p + r) * m + c] = H[(int64_t)(kq + r) * ld + c];
+}
+
+// Energy weights of an augmented pair by virtual block q = 2 [a is a SOMO] +
+// [b is a SOMO]: E_P = sum_ab wd(q) V_ab T_ab + wx(q) V_ab T_ba with
+//   (i alpha, j beta): 3/8 V_ab T_ab over a alpha, b beta; 1/8 V_ab T_ba over a beta, b alpha
+//   (j alpha, i beta): the same with the roles of a and b exchanged
+//   same spin sigma:   1/4 V_ab (T_ab - T_ba) over a, b both sigma virtuals.
+// Block 0 (both PNOs) gives the plain weights w_alpha, w_beta.
+__device__ __forceinline__ void somo_block_weights(const PairDesc& pd, int q, double& wd,
+                                                   double& wx) {
+  const double c1 = pd.c1, c2 = pd.n_ab - pd.c1, naa = pd.n_aa, nbb = pd.n_bb;
+  if (q == 0) {
+    wd = 3.0 * pd.n_ab / 8.0 + (naa + nbb) / 4.0;
+    wx = pd.n_ab / 8.0 - (naa + nbb) / 4.0;
+  } else if (q == 1) {        // a PNO, b SOMO
+    wd = 3.0 * c1 / 8.0 + nbb / 4.0;
+    wx = c2 / 8.0 - nbb / 4.0;
+  } else if (q == 2) {        // a SOMO, b PNO
+    wd = 3.0 * c2 / 8.0 + nbb / 4.0;
+    wx = c1 / 8.0 - nbb / 4.0;
+  } else {                    // both SOMOs: beta-beta only
+    wd = nbb / 4.0;
+    wx = -nbb / 4.0;
+  }
+}
+
+// Steps 4-5 of an augmented pair: block sums D_q = sum V_ab T_ab and
+// X_q = sum V_ab T_ba over the four virtual blocks (fixed order), then the
+// spin cases.  Every thread returns e[3]; D, X are the unrestricted totals.
+__device__ __forceinline__ void somo_pair_energy(const PairDesc& pd, const double* V,
+                                                 const double* T, double (*red)[kThreads / 32],
+                                                 double e[3], double& D, double& X) {
+  const int k = pd.k, kq = pd.k - pd.s;
+  double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0, x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
+  for (int el = threadIdx.x; el < k * k; el += kThreads) {
+    const int a = el / k, b = el - a * k;
+    const double v = V[el];
+    const double td = v * T[el], tx = v * T[b * k + a];
+    if (a < kq) {
+      if (b < kq) { d0 += td; x0 += tx; } else { d1 += td; x1 += tx; }
+    } else {
+      if (b < kq) { d2 += td; x2 += tx; } else { d3 += td; x3 += tx; }
+    }
+  }
+  cta_sum2(d0, x0, red);
+  cta_sum2(d1, x1, red);
+  cta_sum2(d2, x2, red);
+  cta_sum2(d3, x3, red);
+  const double c1 = pd.c1, c2 = pd.n_ab - pd.c1;
+  // (i alpha, j beta): a in PNOs, b anywhere for D; a anywhere, b in PNOs for X
+  e[0] = c1 * (3.0 * (d0 + d1) + (x0 + x2)) / 8.0 + c2 * (3.0 * (d0 + d2) + (x0 + x1)) / 8.0;
+  e[1] = pd.n_aa * (d0 - x0) / 4.0;
+  D = ((d0 + d1) + d2) + d3;
+  X = ((x0 + x1) + x2) + x3;
+  e[2] = pd.n_bb * (D - X) / 4.0;
+}
+
 }  // namespace pf12

@@ -21,6 +21,16 @@ namespace pf12 {
 //   M = [J_g ; At^g_i ; At^g_j]   ((m + 2k) x ld)  ->  [L ; Ct_i ; Ct_j]
 //   F = [At^f_i ; At^f_j]         (2k x ld)        ->  [At^f_i - Ct_i J_f ; At^f_j]
 //   V = (At^f_i - Ct_i J_f) Ct_j^T + Ct_i At^f_j^T
+__device__ __forceinline__ void write_pair_energy(const FwdParams& prm, int64_t P, const double e[3],
+                                                  double D, double X) {
+  prm.e_pair[3 * P + 0] = e[0];
+  prm.e_pair[3 * P + 1] = e[1];
+  prm.e_pair[3 * P + 2] = e[2];
+  prm.dx[2 * P] = D;
+  prm.dx[2 * P + 1] = X;
+  prm.status[P] = (isfinite(D) && isfinite(X)) ? 0 : 2;
+}
+
 template <typename TC>
 __device__ bool pair_forward(const FwdParams& prm, const PairDesc& pd, double* ws, GemmSmem& gs,
                              CholSmem& cs, double (*red)[kThreads / 32], SieveCtl& sc,
@@ -49,10 +59,15 @@ __device__ bool pair_forward(const FwdParams& prm, const PairDesc& pd, double* w
     for (int x = 0; x < 4; ++x) Asrc[x] = G + (int64_t)x * p * m;
   }
   // S1': At^x = Q^T A^x  (k x m), A(a, mu) = Q[mu * k + a]
+  // SOMO-augmented pair: the first kq rows through Q, the SOMO rows copied
+  const int kq = k - pd.s;
   double* Adst[4] = {M + (int64_t)m * ld, M + (int64_t)(m + k) * ld, F, F + (int64_t)k * ld};
 #pragma unroll 1
-  for (int x = 0; x < 4; ++x)
-    cta_gemm<TC, true, false>(k, m, p, Q, k, Asrc[x], m, Adst[x], ld, 1.0, false, gs);
+  for (int x = 0; x < 4; ++x) {
+    cta_gemm<TC, true, false>(kq, m, p, Q, kq, Asrc[x], m, Adst[x], ld, 1.0, false, gs);
+    if (pd.s) copy_somo_rows(Asrc[x], p, pd.s, m, Adst[x], ld, kq);
+  }
+  if (pd.s) __syncthreads();
 
   // S2: FP64 Cholesky of J_g with the forward solve of [At^g_i; At^g_j]
   const bool ok = chol_augmented(M, ld, m, m + 2 * k, cs, gs);
@@ -84,6 +99,12 @@ __device__ bool pair_forward(const FwdParams& prm, const PairDesc& pd, double* w
       cta_gemm_tile<TC, false, true>(k, k, m, Ci, ld, Fj, ld, V, k, r0, c0, 1.0, true, gs);
     }
   __syncthreads();
+  if (pd.s) {   // augmented pair: spin cases restricted to their own virtuals
+    double e[3], D, X;
+    somo_pair_energy(pd, V, T, red, e, D, X);
+    if (tid == 0) write_pair_energy(prm, pd.pair, e, D, X);
+    return true;
+  }
 
   // S4: d = <V, T>, x = <V, T^T>   (FP64, fixed order)
   double sd = 0.0, sx = 0.0;
@@ -164,12 +185,15 @@ __device__ bool pair_forward_tc(const FwdParams& prm, const PairDesc& pd, double
     if (!sieve_pair(prm, pd, G, gs, sc, phase)) return false;
     for (int x = 0; x < 4; ++x) Asrc[x] = G + (int64_t)x * p * m;
   }
+  const int kq = k - pd.s;
   double* Adst[4] = {M + (int64_t)m * ld, M + (int64_t)(m + k) * ld, F, F + (int64_t)k * ld};
 #pragma unroll 1
-  for (int x = 0; x < 4; ++x)
-    if (!tc::gemm<true, true>(m, k, p, Asrc[x], m, Q, k, Adst[x], ld, 1.0, false, st, ctrl, s_flag,
+  for (int x = 0; x < 4; ++x) {
+    if (!tc::gemm<true, true>(m, kq, p, Asrc[x], m, Q, kq, Adst[x], ld, 1.0, false, st, ctrl, s_flag,
                               prm.debug_wait_polls))
       return false;
+    if (pd.s) copy_somo_rows(Asrc[x], p, pd.s, m, Adst[x], ld, kq);
+  }
   __syncthreads();
   const bool ok = chol_augmented(M, ld, m, m + 2 * k, cs, gs);
   if (!ok) {
@@ -198,6 +222,12 @@ __device__ bool pair_forward_tc(const FwdParams& prm, const PairDesc& pd, double
       cta_gemm_tile<float, false, true>(k, k, m, Ci, ld, Fj, ld, V, k, r0, c0, 1.0, true, gs);
     }
   __syncthreads();
+  if (pd.s) {
+    double e[3], D, X;
+    somo_pair_energy(pd, V, T, red, e, D, X);
+    if (tid == 0) write_pair_energy(prm, pd.pair, e, D, X);
+    return true;
+  }
   double sd = 0.0, sx = 0.0;
   for (int e = tid; e < k * k; e += kThreads) {
     const int a = e / k, b = e - a * k;
@@ -489,7 +519,8 @@ extern "C" int pf12_energy_noalloc(int32_t n_orb, const int8_t* kind, int64_t n_
       }
       d.w_alpha = 3.0f * d.n_ab / 8.0f + (d.n_aa + d.n_bb) / 4.0f;
       d.w_beta = d.n_ab / 8.0f - (d.n_aa + d.n_bb) / 4.0f;
-      d.pad = 0;
+      d.c1 = (int8_t)(kind[pj[P]] == 0);
+      d.s = 0;
     }
     // pageable source: the copy has consumed `stage` when the call returns
     if (cudaMemcpyAsync(base + off_desc + sizeof(PairDesc) * P0, stage, sizeof(PairDesc) * nb,

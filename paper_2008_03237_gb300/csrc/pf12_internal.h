@@ -13,12 +13,17 @@ constexpr int kMaxAux = 4096;   // m limit (workspace and index arithmetic in in
 constexpr int kMaxPno = 256;    // k limit
 
 // One entry per pair, in the persistent kernel's (cost-sorted) order.
+// SOMO-augmented pairs (s > 0): the factor blocks have p + s rows (the s SOMO
+// rows last), Q is p x (k - s), and V, T are k x k with the SOMO virtuals last.
 struct PairDesc {
   int64_t off_pm, off_mm, off_pk, off_kk;  // element offsets into the packed inputs
-  int32_t p, k, m, pair;                   // sizes and the pair's index in the caller's list
+  int32_t p, k, m, pair;                   // PAO rows, virtual dimension, aux size, caller's index
   float w_alpha, w_beta;                   // E_P = w_alpha d + w_beta x (as FP64 below)
-  int8_t n_ab, n_aa, n_bb, pad;            // spin-case multiplicities
+  int8_t n_ab, n_aa, n_bb;                 // spin-case multiplicities
+  int8_t c1;                               // 1 if (i alpha, j beta) is occupied; c2 = n_ab - c1
+  int32_t s;                               // SOMO rows / virtuals of the augmented space (0: none)
 };
+static_assert(sizeof(PairDesc) == 64, "PairDesc layout");
 
 // Gather mode: where pair P's factors live inside the per-orbital blocks.
 struct GatherDesc {
