@@ -169,8 +169,42 @@ int pf12_upload_pairs(pf12_ctx* ctx, int32_t n_orb, const int8_t* orb_kind, int6
  * captured CUDA graph after the first call): projections, FP64 Cholesky of
  * J_g, FP64 solves, robust fit to V (kept in the context), and the pair
  * contractions d, x.  A pair whose J_g is not SPD gets status NOT_SPD and NaN
- * energies; the call itself still returns 0 (query pf12_pair_status). */
+ * energies; the call itself still returns 0 (query pf12_pair_status).
+ * With streamed inputs (pf12_set_arrival) the launch is direct, not from the
+ * graph. */
 int pf12_fit(pf12_ctx* ctx);
+
+/* Streamed inputs for the next pf12_fit calls: the fit may start before the
+ * inputs have reached the device.  No counterpart in the paper, which streams
+ * pair integrals from disk on the CPU; here the host-to-device copies of one
+ * pair list overlap its single persistent launch, so copying and computing
+ * run at the same time without a launch (and its tail) per batch.
+ *   n_groups: number of arrival groups; 0 turns streaming off (the queue goes
+ *     back to the plain cost order).
+ *   group_end (host, n_groups): group g holds the pairs [group_end[g-1],
+ *     group_end[g]) of the caller's list (group_end[-1] = 0); strictly
+ *     increasing, last entry n_pairs.
+ *   ready_dev (device, n_groups uint32, 4-byte aligned, caller-owned): the
+ *     caller writes ready_dev[g] = epoch once every input block of group g's
+ *     pairs is on the device, with a copy (cudaMemcpyAsync of 4 bytes) issued
+ *     on its copy stream after that group's copies -- not with a kernel, which
+ *     could wait behind the persistent launch for a free SM.  Issue the copies
+ *     before pf12_fit (or on a stream that runs concurrently with it), and
+ *     after this call, which reorders the queue with small copies from
+ *     pageable memory on the context's stream.
+ *   epoch: the value that marks this call's data (change it every call, e.g.
+ *     a counter; comparison is wrap-safe).
+ * The queue is ordered group by group (longest pair first within a group);
+ * a CTA waits for a group's flag before its first pair of that group, at most
+ * 60 s (2 ms under pf12_opts.debug_wait_timeout); on expiry the pair gets
+ * status 3, the launch stops taking pairs and pf12_energy returns
+ * PF12_ERR_TIMEOUT (upload again before the next fit).  A context that still
+ * has to time its variants first waits for the last group (expiry: the same
+ * error, with no pair evaluated).  Packed mode only
+ * (gather mode: PF12_ERR_UNSUPPORTED).  A new pf12_upload_pairs clears the
+ * setting; pf12_backward does not wait (call it after the fit). */
+int pf12_set_arrival(pf12_ctx* ctx, int32_t n_groups, const int64_t* group_end,
+                     const uint32_t* ready_dev, uint32_t epoch);
 
 /* Copy V^{ij} of every pair (k x k, row-major) into V_dev at the pair's off_kk
  * offset (same layout as T).  Requires a previous pf12_fit. */

@@ -121,6 +121,25 @@ class PairF12:
         self.n_pairs = n
         self.len_kk = tt.len_kk
 
+    def set_arrival(self, group_end, ready, epoch):
+        """Streamed inputs for the next fits (pf12_set_arrival): group_end
+        (host int64, strictly increasing, last = n_pairs) splits the pair list
+        into groups; ready (CUDA int32/uint32 tensor, one flag per group) is
+        set to epoch by the caller's copy stream once a group's inputs are on
+        the device.  An empty group_end turns streaming off."""
+        ends = _i64(group_end)
+        if len(ends) == 0:
+            self._check(self._L.pf12_set_arrival(self._h, 0, None, None, 0))
+            self._arrival = None
+            return
+        if not (ready.is_cuda and ready.dtype in (torch.int32, torch.uint32) and ready.is_contiguous()
+                and ready.numel() >= len(ends)):
+            raise ValueError("ready must be a contiguous int32 CUDA tensor with one flag per group")
+        self._check(self._L.pf12_set_arrival(self._h, len(ends), _ptr(ends, ctypes.c_int64),
+                                             ctypes.c_void_p(ready.data_ptr()),
+                                             int(epoch) & 0xFFFFFFFF))
+        self._arrival = (ends, ready)
+
     def upload_pairs_gather(self, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, blocks, orbitals,
                             maps, tensors, offsets):
         """Gather mode.  blocks: dict Bg, Bf (packed per-orbital float64 CUDA

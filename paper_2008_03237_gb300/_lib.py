@@ -55,6 +55,8 @@ class Stats(ctypes.Structure):
 SIGNATURES = {
     "pf12_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Opts)]),
     "pf12_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "pf12_set_arrival": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, c_i64p, ctypes.c_void_p,
+                                        ctypes.c_uint32]),
     "pf12_upload_pairs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, c_i8p, ctypes.c_int64,
                                          c_i32p, c_i32p, c_i32p, c_i32p, c_i32p,
                                          ctypes.POINTER(Tensors)]),

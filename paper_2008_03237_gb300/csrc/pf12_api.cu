@@ -78,6 +78,16 @@ struct pf12_ctx {
   bool augment = false;            // option: SOMO-augmented PNO space
   uint32_t debug_wait_polls = 0;   // test hook (pf12_opts.debug_wait_timeout)
 
+  // streamed inputs (pf12_set_arrival): the queue is ordered group by group
+  std::vector<PairDesc> h_desc;    // caller order, kept from the upload
+  std::vector<double> h_cost;
+  std::vector<int64_t> arr_end;    // group ends in the caller's pair order
+  const uint32_t* arr_ready = nullptr;
+  uint32_t arr_epoch = 0;
+  bool arr_dirty = false;          // queue order to rebuild before the next fit
+  int32_t* d_slot_group = nullptr;
+  size_t cap_sg = 0;
+
   // graph of the forward launch
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -128,6 +138,9 @@ void free_pairs(pf12_ctx* c) {
   c->variant = -1;
   c->bwd_variant = -1;
   c->n_sample = 0;
+  c->arr_end.clear();
+  c->arr_ready = nullptr;
+  c->arr_dirty = false;
   c->gather = false;
   c->uploaded = c->fitted = false;
   c->n_pairs = 0;
@@ -138,7 +151,7 @@ void release_all(pf12_ctx* c) {
   void* ptrs[] = {c->d_desc, c->d_gdesc, c->d_desc_by_pair, c->d_map_pao, c->d_map_aux,
                   c->d_orb_ptr, c->d_orb_list, c->d_off_orb, c->d_ld_orb, c->d_dA,
                   c->d_desc_sample, c->d_V, c->d_epair, c->d_dx, c->d_status, c->d_out3,
-                  c->d_counter, c->d_work, c->d_tmaps};
+                  c->d_counter, c->d_work, c->d_tmaps, c->d_slot_group};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -395,6 +408,8 @@ static int upload_impl(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n
   std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
   std::vector<PairDesc> sorted(n_pairs);
   for (int64_t s = 0; s < n_pairs; ++s) sorted[s] = desc[order[s]];
+  c->h_desc = desc;
+  c->h_cost = cost;
 
   if (t) c->t = *t;
   c->n_pairs = n_pairs;
@@ -619,6 +634,44 @@ int pf12_upload_pairs_gather(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int
 
 namespace {
 
+// Longest wait for an input group's arrival flag (short under the test hook).
+uint64_t arrival_timeout(const pf12_ctx* c) {
+  return c->debug_wait_polls ? 2000000ull : 60000000000ull;
+}
+
+// Queue order of the persistent launch: longest pair first (ties in list
+// order); with streamed inputs group by group, longest first within a group,
+// plus the group of every queue slot.
+int apply_queue_order(pf12_ctx* c) {
+  const int64_t n = c->n_pairs;
+  std::vector<int32_t> group(n, 0);
+  if (c->arr_ready)
+    for (int64_t P = 0, g = 0; P < n; ++P) {
+      while (P >= c->arr_end[g]) ++g;
+      group[P] = (int32_t)g;
+    }
+  std::vector<int64_t> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    if (group[a] != group[b]) return group[a] < group[b];
+    return c->h_cost[a] > c->h_cost[b];
+  });
+  std::vector<PairDesc> sorted(n);
+  std::vector<int32_t> slot_group(n);
+  for (int64_t q = 0; q < n; ++q) {
+    sorted[q] = c->h_desc[order[q]];
+    slot_group[q] = group[order[q]];
+  }
+  PF12_CUDA(c, grow(c->d_slot_group, c->cap_sg, (size_t)n));
+  // pageable sources: both copies have consumed the vectors when they return
+  PF12_CUDA(c, cudaMemcpyAsync(c->d_desc, sorted.data(), sizeof(PairDesc) * n,
+                               cudaMemcpyHostToDevice, c->stream));
+  PF12_CUDA(c, cudaMemcpyAsync(c->d_slot_group, slot_group.data(), sizeof(int32_t) * n,
+                               cudaMemcpyHostToDevice, c->stream));
+  c->arr_dirty = false;
+  return PF12_OK;
+}
+
 // Autotuner: time every forward variant on the cost-spread sample of this pair
 // list (one warm-up launch on a single pair, then one timed launch) and keep
 // the fastest; the tensor-core variant only when it wins by 2 %.  Results are cached per (GPU, precision, size signature) in the optional
@@ -646,6 +699,9 @@ int tune(pf12_ctx* c) {
     c->variant = 0;
     return PF12_OK;
   }
+  if (c->arr_ready)   // streamed inputs: the sample spans every group, wait for the last one
+    PF12_CUDA(c, pf12::launch_wait_ready(c->arr_ready, (int32_t)c->arr_end.size(), c->arr_epoch,
+                                         arrival_timeout(c), c->d_counter + 2, c->stream));
   pf12::FwdParams f = fwd_params(c);
   f.desc = c->d_desc_sample;
   int best = 0;
@@ -684,6 +740,34 @@ int tune(pf12_ctx* c) {
 
 extern "C" {
 
+int pf12_set_arrival(pf12_ctx* c, int32_t n_groups, const int64_t* group_end,
+                     const uint32_t* ready_dev, uint32_t epoch) {
+  if (!c) return PF12_ERR_INVALID_ARG;
+  if (!c->uploaded) return fail(c, PF12_ERR_INVALID_ARG, "pf12_set_arrival before pf12_upload_pairs");
+  if (n_groups == 0 || c->n_pairs == 0) {
+    const bool was = c->arr_ready != nullptr;
+    c->arr_ready = nullptr;
+    c->arr_end.clear();
+    return was ? apply_queue_order(c) : PF12_OK;   // back to the plain cost order
+  }
+  if (c->gather) return fail(c, PF12_ERR_UNSUPPORTED, "streamed inputs are available in packed mode only");
+  if (n_groups < 0 || !group_end || !ready_dev || (reinterpret_cast<uintptr_t>(ready_dev) & 3u))
+    return fail(c, PF12_ERR_INVALID_ARG, "n_groups < 0, null group_end, or null / unaligned ready flags");
+  for (int32_t g = 0; g < n_groups; ++g)
+    if (group_end[g] <= (g ? group_end[g - 1] : 0) || group_end[g] > c->n_pairs)
+      return fail(c, PF12_ERR_INVALID_ARG, "group_end must increase strictly within (0, n_pairs]");
+  if (group_end[n_groups - 1] != c->n_pairs)
+    return fail(c, PF12_ERR_INVALID_ARG, "the last group must end at n_pairs");
+  std::vector<int64_t> ends(group_end, group_end + n_groups);
+  const bool reorder = !c->arr_ready || ends != c->arr_end || c->arr_dirty;
+  c->arr_end = ends;
+  c->arr_ready = ready_dev;
+  c->arr_epoch = epoch;
+  // reorder now, before the caller issues its copies: the descriptor copies
+  // come from pageable memory and would otherwise queue behind them
+  return reorder ? apply_queue_order(c) : PF12_OK;
+}
+
 int pf12_fit(pf12_ctx* c) {
   if (!c) return PF12_ERR_INVALID_ARG;
   if (!c->uploaded) return fail(c, PF12_ERR_INVALID_ARG, "pf12_fit before pf12_upload_pairs");
@@ -691,10 +775,30 @@ int pf12_fit(pf12_ctx* c) {
     c->fitted = true;
     return PF12_OK;
   }
+  if (c->arr_dirty) {
+    const int rc = apply_queue_order(c);
+    if (rc != PF12_OK) return rc;
+  }
+  const uint64_t arrival_timeout_ns = arrival_timeout(c);
   if (c->variant < 0) {
     const int rc = tune(c);
     if (rc != PF12_OK) return rc;
     c->n_ctas = c->n_ctas_v[c->variant];
+  }
+  if (c->arr_ready) {
+    // streamed inputs: direct launch (the epoch changes from call to call)
+    pf12::FwdParams f = fwd_params(c);
+    f.ready = c->arr_ready;
+    f.slot_group = c->d_slot_group;
+    f.epoch = c->arr_epoch;
+    f.arrival_timeout_ns = arrival_timeout_ns;
+    PF12_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+    PF12_CUDA(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->stream));
+    PF12_CUDA(c, pf12::launch_forward(f, c->precision, c->variant, c->n_ctas, c->stream));
+    PF12_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+    c->t_fit = true;
+    c->fitted = true;
+    return PF12_OK;
   }
   if (!c->graph_exec) {
     // capture on the library's own stream (nothing executes), replay on the caller's
@@ -752,7 +856,9 @@ int pf12_energy(pf12_ctx* c, double* e_pair_dev, double* E_host) {
   *E_host = out3[0];
   if (out3[3] != 0.0) {
     *E_host = std::nan("");
-    return fail(c, PF12_ERR_TIMEOUT, "a bounded tensor-core wait expired; pairs after it were not evaluated");
+    return fail(c, PF12_ERR_TIMEOUT,
+                "a bounded device wait expired (tensor-core or TMA barrier, or input arrival); "
+                "pairs after it were not evaluated; upload again before the next fit");
   }
   if (out3[1] > 0) {
     char buf[128];

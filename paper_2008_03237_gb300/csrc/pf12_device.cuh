@@ -585,4 +585,51 @@ __device__ __forceinline__ void somo_pair_energy(const PairDesc& pd, const doubl
   e[2] = pd.n_bb * (D - X) / 4.0;
 }
 
+// ---------------------------------------------------------------------------
+// Streamed inputs: bounded wait of one thread for an arrival flag written by a
+// copy on another stream.
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// True once ready[g] has reached epoch (wrap-safe comparison); false when
+// timeout_ns passed first (the poll count is capped as well).
+__device__ __forceinline__ bool wait_ready(const uint32_t* ready, int g, uint32_t epoch,
+                                           uint64_t timeout_ns) {
+  const uint64_t t0 = global_ns();
+  const uint64_t max_polls = timeout_ns / 64 + 1024;
+  const size_t addr = __cvta_generic_to_global(ready + g);
+  for (uint64_t polls = 0;; ++polls) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(addr) : "memory");
+    if ((int32_t)(v - epoch) >= 0) return true;
+    if (polls >= max_polls || global_ns() - t0 > timeout_ns) return false;
+    __nanosleep(128);
+  }
+}
+
+// Thread 0 of the CTA: take the next queue slot; with streamed inputs wait for
+// its group (groups arrive in order, so one wait per new group).  Returns the
+// slot, n_pairs when the queue is done or stopped, or -1 after an expired wait
+// (the pair is marked status 3 and the stop flag set).
+__device__ __forceinline__ long long next_slot(const FwdParams& prm, int& known_group) {
+  long long sl = (prm.err && *prm.err != 0) ? prm.n_pairs : atomicAdd(prm.counter, 1);
+  if (sl < prm.n_pairs && prm.ready) {
+    const int g = prm.slot_group[sl];
+    if (g > known_group) {
+      if (wait_ready(prm.ready, g, prm.epoch, prm.arrival_timeout_ns)) {
+        known_group = g;
+      } else {
+        prm.status[prm.desc[sl].pair] = 3;
+        atomicExch(prm.err, 1);
+        sl = -1;
+      }
+    }
+  }
+  return sl;
+}
+
 }  // namespace pf12

@@ -141,12 +141,13 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_forward_kernel(FwdParams 
   uint32_t phase = 0;
   if (prm.gdesc) sieve_init(sc);
   double* ws = prm.work + (int64_t)blockIdx.x * prm.ws_stride;
+  int known_group = -1;
   for (;;) {
-    if (threadIdx.x == 0) s_slot = (prm.err && *prm.err != 0) ? prm.n_pairs : atomicAdd(prm.counter, 1);
+    if (threadIdx.x == 0) s_slot = next_slot(prm, known_group);
     __syncthreads();
     const long long slot = s_slot;
     __syncthreads();
-    if (slot >= prm.n_pairs) break;
+    if (slot < 0 || slot >= prm.n_pairs) break;
     const PairDesc pd = prm.desc[slot];
     if (!pair_forward<TC>(prm, pd, ws, gs, cs, red, sc, phase)) {
       if (threadIdx.x == 0) {
@@ -272,12 +273,13 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_forward_tc_kernel(FwdPara
   if (threadIdx.x == 0) *s_flag = 0;
   tc::setup(ctrl);
   double* ws = prm.work + (int64_t)blockIdx.x * prm.ws_stride;
+  int known_group = -1;
   for (;;) {
-    if (threadIdx.x == 0) *s_slot = (*prm.err != 0) ? prm.n_pairs : atomicAdd(prm.counter, 1);
+    if (threadIdx.x == 0) *s_slot = next_slot(prm, known_group);
     __syncthreads();
     const long long slot = *s_slot;
     __syncthreads();
-    if (slot >= prm.n_pairs) break;
+    if (slot < 0 || slot >= prm.n_pairs) break;
     const PairDesc pd = prm.desc[slot];
     if (!pair_forward_tc(prm, pd, ws, gs, cs, red, st, ctrl, s_flag, sc, phase)) {
       if (threadIdx.x == 0) {
@@ -404,6 +406,20 @@ __global__ void __launch_bounds__(1024) energy_total_kernel(const double* e_pair
 cudaError_t launch_energy_total(const double* e_pair, const int32_t* status, int64_t n_pairs,
                                 const int32_t* err, double* out3, cudaStream_t s) {
   energy_total_kernel<<<1, 1024, 0, s>>>(e_pair, status, n_pairs, err, out3);
+  return cudaGetLastError();
+}
+
+// Streamed inputs, before the autotuner's sample launches (whose pairs come
+// from every group): one thread waits for the last group, which arrives last.
+__global__ void wait_ready_kernel(const uint32_t* ready, int32_t n_groups, uint32_t epoch,
+                                  uint64_t timeout_ns, int32_t* err) {
+  if (threadIdx.x == 0 && n_groups > 0 && !wait_ready(ready, n_groups - 1, epoch, timeout_ns))
+    atomicExch(err, 1);
+}
+
+cudaError_t launch_wait_ready(const uint32_t* ready, int32_t n_groups, uint32_t epoch,
+                              uint64_t timeout_ns, int32_t* err, cudaStream_t s) {
+  wait_ready_kernel<<<1, 32, 0, s>>>(ready, n_groups, epoch, timeout_ns, err);
   return cudaGetLastError();
 }
 

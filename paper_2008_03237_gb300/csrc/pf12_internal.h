@@ -55,6 +55,15 @@ struct FwdParams {
   // test hook: nonzero = issue no tensor-core / TMA work before the first
   // barrier wait and give that wait this many polls, so it expires
   uint32_t debug_wait_polls;
+  // streamed inputs (ready == null: every input is resident before the
+  // launch).  The pair in queue slot s belongs to arrival group slot_group[s];
+  // a CTA reads that pair's inputs only after ready[group] has reached epoch
+  // (written by the caller's copy stream after the group's copies), waiting at
+  // most arrival_timeout_ns.
+  const uint32_t* ready;
+  const int32_t* slot_group;
+  uint32_t epoch;
+  uint64_t arrival_timeout_ns;
 };
 
 struct BwdParams {
@@ -94,6 +103,10 @@ cudaError_t launch_forward(const FwdParams& prm, int precision, int variant, int
 constexpr int kBwdVariants = 2;
 cudaError_t launch_backward(const BwdParams& prm, int precision, int variant, int n_ctas,
                             cudaStream_t s);
+// One warp waits (bounded) until every ready[g], g < n_groups, has reached
+// epoch; sets *err on expiry.
+cudaError_t launch_wait_ready(const uint32_t* ready, int32_t n_groups, uint32_t epoch,
+                              uint64_t timeout_ns, int32_t* err, cudaStream_t s);
 cudaError_t launch_energy_total(const double* e_pair, const int32_t* status, int64_t n_pairs,
                                 const int32_t* err, double* out3, cudaStream_t s);
 int forward_blocks_per_sm(int precision, int variant);

@@ -110,7 +110,10 @@ def run_from_host(eng, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, host, layou
     The pair list is cut into batches under budget_bytes; batch b + 1's slices
     are copied host -> device on a separate stream into the other of two device
     slots while batch b is fitted on the current stream, so copies overlap the
-    compute.  eng is a PairF12 context, reused across calls (its device
+    compute.  Batch b + 1's copies are issued after batch b's upload: the
+    upload copies its small descriptor arrays from pageable memory on the
+    compute stream, and queued behind a batch-sized copy that small copy
+    would hold the fit back until the next batch had arrived.  eng is a PairF12 context, reused across calls (its device
     buffers and tuned variant carry over).  Returns (E, e_pair (device,
     n x 3), status, number of batches)."""
     n = len(pi)
@@ -149,13 +152,13 @@ def run_from_host(eng, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, host, layou
     totals = []
     issue(0)
     for q, (b, e) in enumerate(batches):
-        if q + 1 < len(batches):
-            issue(q + 1)
         compute.wait_event(copied[q])
         lay_b = {"off_" + key: np.asarray(layout["off_" + key][b:e]) - ranges[q][key][0]
                  for key in ("pm", "mm", "pk", "kk")}
         eng.upload_pairs(n_orb, orb_kind, pi[b:e], pj[b:e], n_pao[b:e], n_pno[b:e], n_aux[b:e],
                          slots[q % 2], lay_b)
+        if q + 1 < len(batches):
+            issue(q + 1)
         eng.fit()
         Eb, _ = eng.energy(e_pair[b:e], check=False)
         totals.append(Eb)
@@ -166,3 +169,102 @@ def run_from_host(eng, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, host, layou
     for x in totals:
         E += x
     return E, e_pair[:n], status, len(batches)
+
+
+def arrival_groups(n_pao, n_pno, n_aux, first_bytes=0.5e9, max_bytes=4e9, n_somo_aug=0):
+    """Contiguous pair groups for streamed inputs: the first group holds about
+    first_bytes of inputs and each next one twice the previous, up to
+    max_bytes, so the launch starts early and the copies stay ahead of it.
+    Returns the group ends (int64, last = n_pairs)."""
+    p = np.asarray(n_pao, np.float64) + n_somo_aug
+    k = np.asarray(n_pno, np.float64)
+    m = np.asarray(n_aux, np.float64)
+    v = k + n_somo_aug
+    per = 8.0 * (4 * p * m + 2 * m * m + (p - n_somo_aug) * k + v * v)
+    ends, acc, cap = [], 0.0, float(first_bytes)
+    for P, b in enumerate(per):
+        if acc > 0 and acc + b > cap:
+            ends.append(P)
+            acc, cap = 0.0, min(2 * cap, float(max_bytes))
+        acc += b
+    if len(per):
+        ends.append(len(per))
+    return np.asarray(ends, np.int64)
+
+
+class HostStreamer:
+    """End-to-end evaluation of a pair list whose packed inputs sit in pinned
+    host memory, with one persistent launch per call.
+
+    Every call copies the inputs group by group (arrival_groups) on a copy
+    stream into device buffers owned by this object and, after each group,
+    writes that group's arrival flag with a 4-byte copy; the fit is launched
+    at once and its CTAs wait for a group's flag before its first pair
+    (pf12_set_arrival).  Copies and compute overlap without a launch, and a
+    queue tail, per batch.  eng is a PairF12 context, reused across calls."""
+
+    def __init__(self, eng, first_bytes=0.5e9, max_group_bytes=4e9):
+        self.eng = eng
+        self.first_bytes = float(first_bytes)
+        self.max_group_bytes = float(max_group_bytes)
+        self.dev = {}
+        self.copy_stream = torch.cuda.Stream()
+        self.epoch = 0
+        self.epoch_host = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+        self.ready = None
+
+    def _buffers(self, host):
+        for x, h in host.items():
+            if x not in self.dev or self.dev[x].numel() < h.numel():
+                self.dev[x] = torch.empty(h.numel(), dtype=torch.float64, device="cuda")
+        return self.dev
+
+    def run(self, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, host, layout):
+        """host: dict of pinned packed float64 tensors (Agi ... T) in the
+        layout of `layout` (off_pm/off_mm/off_pk/off_kk).  Returns (E,
+        e_pair (device, n x 3), status, number of groups)."""
+        eng = self.eng
+        n = len(pi)
+        s_aug = int(np.sum(np.asarray(orb_kind) == 1)) if getattr(eng, "augment_somo", False) else 0
+        ends = arrival_groups(n_pao, n_pno, n_aux, self.first_bytes, self.max_group_bytes, s_aug)
+        dev = self._buffers(host)
+        if self.ready is None or self.ready.numel() < max(len(ends), 1):
+            self.ready = torch.zeros(max(len(ends), 1), dtype=torch.int32, device="cuda")
+        # block ends per tensor kind: pair P's blocks end at off + size
+        rows = np.asarray(n_pao, np.int64) + s_aug
+        virt = np.asarray(n_pno, np.int64) + s_aug
+        m = np.asarray(n_aux, np.int64)
+        sizes = {"pm": rows * m, "mm": m * m, "pk": np.asarray(n_pao, np.int64) * np.asarray(n_pno, np.int64),
+                 "kk": virt * virt}
+        kinds = {"Agi": "pm", "Agj": "pm", "Afi": "pm", "Afj": "pm", "Jg": "mm", "Jf": "mm",
+                 "Q": "pk", "T": "kk"}
+        block_end = {key: np.asarray(layout["off_" + key], np.int64) + sizes[key] for key in sizes}
+        for key, be in block_end.items():   # groups are copied as contiguous ranges
+            if len(be) > 1 and (np.diff(np.asarray(layout["off_" + key], np.int64)) < 0).any():
+                raise ValueError("HostStreamer needs blocks laid out in pair order")
+        compute = torch.cuda.current_stream()
+        # metadata first (small copies from pageable memory on the compute stream)
+        eng.upload_pairs(n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, dev, layout)
+        if n == 0:
+            eng.fit()
+            E, e_pair = eng.energy(check=False)
+            return E, e_pair, np.zeros(0, np.int32), 0
+        self.epoch = (self.epoch + 1) & 0x7FFFFFFF
+        eng.set_arrival(ends, self.ready, self.epoch)
+        self.epoch_host[0] = self.epoch
+        self.copy_stream.wait_stream(compute)    # device buffers free (previous fit done)
+        with torch.cuda.stream(self.copy_stream):
+            beg = {key: 0 for key in sizes}
+            for g, e in enumerate(ends):
+                for x, key in kinds.items():
+                    s0, s1 = beg[key], int(block_end[key][e - 1])
+                    if s1 > s0:
+                        dev[x][s0:s1].copy_(host[x][s0:s1], non_blocking=True)
+                for key in sizes:
+                    beg[key] = int(block_end[key][e - 1])
+                self.ready[g:g + 1].copy_(self.epoch_host, non_blocking=True)
+        eng.fit()
+        E, e_pair = eng.energy(check=False)
+        status = eng.pair_status()
+        compute.wait_stream(self.copy_stream)
+        return E, e_pair, status, len(ends)

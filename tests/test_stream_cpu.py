@@ -28,3 +28,20 @@ def test_plan_batches_covers_list_within_budget():
     assert per.sum() > 800e9 and len(batches) >= 20
     with pytest.raises(ValueError):
         plan_batches(wl.n_pao, wl.n_pno, wl.n_aux, per.max() / 2)
+
+
+def test_arrival_groups_cover_the_list_and_grow():
+    from paper_2008_03237_gb300.stream import arrival_groups
+    wl = S.c160h321()
+    per = input_bytes(wl.n_pao, wl.n_pno, wl.n_aux)
+    ends = arrival_groups(wl.n_pao, wl.n_pno, wl.n_aux, 0.5e9, 4e9)
+    assert ends[-1] == wl.n_pairs and (np.diff(ends) > 0).all() and ends[0] > 0
+    starts = np.concatenate([[0], ends[:-1]])
+    sizes = np.array([per[b:e].sum() for b, e in zip(starts, ends)])
+    assert sizes[0] <= 0.5e9 + per.max()
+    assert sizes[:-1].max() <= 4e9 + per.max()
+    # doubling until the cap: few groups for 178 GB
+    assert 40 <= len(ends) <= 60
+    assert arrival_groups([], [], [], 1e9, 4e9).size == 0
+    one = arrival_groups(wl.n_pao[:1], wl.n_pno[:1], wl.n_aux[:1], 1.0, 1.0)
+    assert list(one) == [1]
