@@ -97,13 +97,20 @@ typedef struct {
                               the PNOs, beta virtuals the PNOs and SOMOs, and each spin case
                               sums over its own virtuals.  Packed mode only (gather mode:
                               PF12_ERR_UNSUPPORTED); k + n_s <= 256.  0: plain PNO space */
+  int metric_packed;       /* 1: Jg and Jf blocks are packed lower triangles, m (m + 1) / 2
+                              doubles at off_mm[P]: row r holds J[r][0..r] at r (r + 1) / 2.
+                              The metrics are symmetric, so this halves their share of the
+                              inputs (the bulk of them) in memory and in host-to-device
+                              copies; the library unpacks J_f into its workspace (m x m per
+                              CTA more).  0: full row-major m x m blocks */
 } pf12_opts;
 
 /* Packed ("plain mode") per-pair tensors.  Pair P's blocks start at element
  * offset off_xx[P] of the matching buffer:
  *   Ag_i, Ag_j, Af_i, Af_j : p x m   at off_pm[P]  (DF factors of orbital i / j,
  *                                                   Coulomb g and F12 f kernels)
- *   Jg, Jf                 : m x m   at off_mm[P]  (SPD auxiliary metrics)
+ *   Jg, Jf                 : m x m   at off_mm[P]  (SPD auxiliary metrics; packed
+ *                                                   lower triangles with metric_packed)
  *   Q                      : p x k   at off_pk[P]  (PAO -> PNO coefficients)
  *   T                      : k x k   at off_kk[P]  (PNO amplitudes t^{ab}_{ij})
  * Offsets are host arrays, element (not byte) offsets, multiples of 2 (16-byte
@@ -187,7 +194,8 @@ int pf12_fit(pf12_ctx* ctx);
  *   ready_dev (device, n_groups uint32, 4-byte aligned, caller-owned): the
  *     caller writes ready_dev[g] = epoch once every input block of group g's
  *     pairs is on the device, with a copy (cudaMemcpyAsync of 4 bytes) issued
- *     on its copy stream after that group's copies -- not with a kernel, which
+ *     on the copy stream of that group's copies, after them (groups may use
+ *     several streams and land in any order) -- not with a kernel, which
  *     could wait behind the persistent launch for a free SM.  Issue the copies
  *     before pf12_fit (or on a stream that runs concurrently with it), and
  *     after this call, which reorders the queue with small copies from
@@ -199,7 +207,7 @@ int pf12_fit(pf12_ctx* ctx);
  * 60 s (2 ms under pf12_opts.debug_wait_timeout); on expiry the pair gets
  * status 3, the launch stops taking pairs and pf12_energy returns
  * PF12_ERR_TIMEOUT (upload again before the next fit).  A context that still
- * has to time its variants first waits for the last group (expiry: the same
+ * has to time its variants first waits for every group (expiry: the same
  * error, with no pair evaluated).  Packed mode only
  * (gather mode: PF12_ERR_UNSUPPORTED).  A new pf12_upload_pairs clears the
  * setting; pf12_backward does not wait (call it after the fit). */

@@ -56,17 +56,22 @@ class PairF12:
     energy sums in both."""
 
     def __init__(self, precision="fp64", workspace_bytes=0, stream=None, tuner_cache=None,
-                 variant=None, sieve_plain=False, debug_wait_timeout=False, augment_somo=False):
+                 variant=None, sieve_plain=False, debug_wait_timeout=False, augment_somo=False,
+                 metric_packed=False):
         """variant: None = autotune, else 0 / 1 (SIMT, 2 / 3 CTAs per SM) or
         2 (tcgen05 tensor-core contractions, mixed precision only).
         augment_somo: SOMO-augmented PNO space (factor blocks (p + n_s) x m with
-        the SOMO rows last, Q p x k, T and V (k + n_s) square)."""
+        the SOMO rows last, Q p x k, T and V (k + n_s) square).
+        metric_packed: Jg, Jf given as packed lower triangles (m (m + 1) / 2
+        per pair)."""
         self._L = lib()
         self._cache = tuner_cache.encode() if tuner_cache else None
         opts = _lib.Opts(_lib.PRECISION[precision], None, int(workspace_bytes), 1, self._cache,
                          -1 if variant is None else int(variant), int(bool(sieve_plain)),
-                         int(bool(debug_wait_timeout)), int(bool(augment_somo)))
+                         int(bool(debug_wait_timeout)), int(bool(augment_somo)),
+                         int(bool(metric_packed)))
         self.augment_somo = bool(augment_somo)
+        self.metric_packed = bool(metric_packed)
         h = ctypes.c_void_p()
         self._check(self._L.pf12_create(ctypes.byref(h), ctypes.byref(opts)), None)
         self._h = h

@@ -21,7 +21,7 @@ class Opts(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t), ("deterministic", ctypes.c_int),
                 ("tuner_cache", ctypes.c_char_p), ("force_variant", ctypes.c_int),
                 ("sieve_plain", ctypes.c_int), ("debug_wait_timeout", ctypes.c_int),
-                ("augment_somo", ctypes.c_int)]
+                ("augment_somo", ctypes.c_int), ("metric_packed", ctypes.c_int)]
 
 
 class Tensors(ctypes.Structure):

@@ -76,6 +76,7 @@ struct pf12_ctx {
   bool use_tma = false;
   bool sieve_plain = false;        // option: sieve with plain loads only
   bool augment = false;            // option: SOMO-augmented PNO space
+  bool packed = false;             // option: metrics as packed lower triangles
   uint32_t debug_wait_polls = 0;   // test hook (pf12_opts.debug_wait_timeout)
 
   // streamed inputs (pf12_set_arrival): the queue is ordered group by group
@@ -192,6 +193,7 @@ pf12::FwdParams fwd_params(pf12_ctx* c) {
   f.counter = c->d_counter;
   f.err = c->d_counter + 2;
   f.debug_wait_polls = c->debug_wait_polls;
+  f.metric_packed = c->packed ? 1 : 0;
   if (c->gather) {
     f.tmaps = c->use_tma ? c->d_tmaps : nullptr;
     f.gdesc = c->d_gdesc;
@@ -227,6 +229,7 @@ int pf12_create(pf12_ctx** out, const pf12_opts* o) {
     c->forced = o->force_variant;
     c->sieve_plain = o->sieve_plain != 0;
     c->augment = o->augment_somo != 0;
+    c->packed = o->metric_packed != 0;
     c->debug_wait_polls = o->debug_wait_timeout ? 4096u : 0u;
   }
   int dev = 0;
@@ -329,7 +332,8 @@ static int upload_impl(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n
       return fail(c, PF12_ERR_INVALID_ARG, buf);
     }
     const int64_t offs[4] = {t->off_pm[P], t->off_mm[P], t->off_pk[P], t->off_kk[P]};
-    const int64_t sizes[4] = {(int64_t)pr * m, (int64_t)m * m, (int64_t)p * kq, (int64_t)k * k};
+    const int64_t mm = c->packed ? (int64_t)m * (m + 1) / 2 : (int64_t)m * m;
+    const int64_t sizes[4] = {(int64_t)pr * m, mm, (int64_t)p * kq, (int64_t)k * k};
     const int64_t lens[4] = {t->len_pm, t->len_mm, t->len_pk, t->len_kk};
     for (int q = 0; q < 4; ++q)
       if (offs[q] < 0 || (offs[q] & 1) || offs[q] + sizes[q] > lens[q]) {
@@ -365,9 +369,9 @@ static int upload_impl(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n
     cost[P] = c64 + cmix / 8.0;
     f64 += c64;
     fmix += cmix;
-    bytes += 8.0 * (4.0 * dpr * dm + 2.0 * dm * dm + dp * dkq + dk * dk);
-    max_fwd = std::max(max_fwd, pf12::fwd_ws(p, k, m, gm));
-    max_bwd = std::max(max_bwd, pf12::bwd_ws(p, k, m, gm));
+    bytes += 8.0 * (4.0 * dpr * dm + 2.0 * (double)mm + dp * dkq + dk * dk);
+    max_fwd = std::max(max_fwd, pf12::fwd_ws(p, k, m, gm, c->packed));
+    max_bwd = std::max(max_bwd, pf12::bwd_ws(p, k, m, gm, c->packed));
     c->off_kk[P] = offs[3];
     c->pk[P] = k;
     if (gm) {
@@ -699,7 +703,7 @@ int tune(pf12_ctx* c) {
     c->variant = 0;
     return PF12_OK;
   }
-  if (c->arr_ready)   // streamed inputs: the sample spans every group, wait for the last one
+  if (c->arr_ready)   // streamed inputs: the sample spans every group: wait for all of them
     PF12_CUDA(c, pf12::launch_wait_ready(c->arr_ready, (int32_t)c->arr_end.size(), c->arr_epoch,
                                          arrival_timeout(c), c->d_counter + 2, c->stream));
   pf12::FwdParams f = fwd_params(c);

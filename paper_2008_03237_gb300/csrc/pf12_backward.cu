@@ -48,8 +48,15 @@ __device__ bool pair_backward(const BwdParams& b, const PairDesc& pd, double* ws
     Afj = G + 3 * (int64_t)p * m;
   }
 
-  for (int r = tid >> 5; r < m; r += kThreads / 32)
-    for (int c = tid & 31; c < m; c += 32) M[(int64_t)r * ld + c] = Jg[(int64_t)r * m + c];
+  load_metric(Jg, m, prm.metric_packed, M, ld);
+  const double* Jf_use = Jf;
+  int64_t ld_jf = m;
+  if (prm.metric_packed) {   // full J_f for its product, unpacked into the slab
+    double* W = ws + bwd_jf_off(p, k, m, prm.gdesc != nullptr);
+    unpack_metric(Jf, m, W, ld);
+    Jf_use = W;
+    ld_jf = ld;
+  }
   // SOMO-augmented pair: Q_aug = blockdiag(Q, I), Q is p x kq
   const int s = pd.s, kq = k - s;
   cta_gemm<TC, true, false>(kq, m, p, Q, kq, Agi, m, M + (int64_t)m * ld, ld, 1.0, false, gs);
@@ -75,7 +82,7 @@ __device__ bool pair_backward(const BwdParams& b, const PairDesc& pd, double* ws
   // R = At^f - Ct J_f  (both x at once: Ct_i, Ct_j are consecutive rows)
   for (int64_t e = tid; e < 2 * (int64_t)k * ld; e += kThreads) R[e] = F[e];
   __syncthreads();
-  cta_gemm<TC, false, false>(2 * k, m, m, Ci, ld, Jf, m, R, ld, -1.0, true, gs);
+  cta_gemm<TC, false, false>(2 * k, m, m, Ci, ld, Jf_use, ld_jf, R, ld, -1.0, true, gs);
 
   // V = R_i Ct_j^T + Ct_i At^f_j^T
   for (int r0 = 0; r0 < k; r0 += kTile)

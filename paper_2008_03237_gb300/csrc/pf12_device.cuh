@@ -612,7 +612,8 @@ __device__ __forceinline__ bool wait_ready(const uint32_t* ready, int g, uint32_
 }
 
 // Thread 0 of the CTA: take the next queue slot; with streamed inputs wait for
-// its group (groups arrive in order, so one wait per new group).  Returns the
+// its group's flag.  A CTA's slots only grow, so its groups never go back and
+// it polls once per new group; groups may land in any order.  Returns the
 // slot, n_pairs when the queue is done or stopped, or -1 after an expired wait
 // (the pair is marked status 3 and the stop flag set).
 __device__ __forceinline__ long long next_slot(const FwdParams& prm, int& known_group) {
@@ -630,6 +631,39 @@ __device__ __forceinline__ long long next_slot(const FwdParams& prm, int& known_
     }
   }
   return sl;
+}
+
+// ---------------------------------------------------------------------------
+// Auxiliary metrics as full row-major blocks or as packed lower triangles
+// (row r holds J[r][0..r] at r (r + 1) / 2): a symmetric metric then travels
+// and rests in about half the bytes.
+
+// J_g into the top m rows of M (row stride ld).  Packed: the lower triangle
+// only, which is all the Cholesky reads.
+__device__ __forceinline__ void load_metric(const double* J, int m, bool packed, double* M,
+                                            int64_t ld) {
+  const int lane = threadIdx.x & 31;
+  for (int r = threadIdx.x >> 5; r < m; r += kThreads / 32) {
+    if (packed) {
+      const double* row = J + (int64_t)r * (r + 1) / 2;
+      for (int c = lane; c <= r; c += 32) M[(int64_t)r * ld + c] = row[c];
+    } else {
+      for (int c = lane; c < m; c += 32) M[(int64_t)r * ld + c] = J[(int64_t)r * m + c];
+    }
+  }
+}
+
+// Full symmetric m x m J_f (row stride ld) from its packed lower triangle.
+__device__ __forceinline__ void unpack_metric(const double* J, int m, double* W, int64_t ld) {
+  const int lane = threadIdx.x & 31;
+  for (int r = threadIdx.x >> 5; r < m; r += kThreads / 32) {
+    const double* row = J + (int64_t)r * (r + 1) / 2;
+    for (int c = lane; c <= r; c += 32) {
+      const double v = row[c];
+      W[(int64_t)r * ld + c] = v;
+      W[(int64_t)c * ld + r] = v;
+    }
+  }
 }
 
 }  // namespace pf12

@@ -45,9 +45,16 @@ __device__ bool pair_forward(const FwdParams& prm, const PairDesc& pd, double* w
   const double* Q = prm.Q + pd.off_pk;
   const double* T = prm.T + pd.off_kk;
 
-  // J_g -> M (rows of m contiguous doubles)
-  for (int r = tid >> 5; r < m; r += kThreads / 32)
-    for (int c = tid & 31; c < m; c += 32) M[(int64_t)r * ld + c] = Jg[(int64_t)r * m + c];
+  // J_g -> M; a packed J_f is unpacked into the slab for its product
+  load_metric(Jg, m, prm.metric_packed, M, ld);
+  const double* Jf_use = Jf;
+  int64_t ld_jf = m;
+  if (prm.metric_packed) {
+    double* W = ws + fwd_jf_off(p, k, m, prm.gdesc != nullptr);
+    unpack_metric(Jf, m, W, ld);
+    Jf_use = W;
+    ld_jf = ld;
+  }
 
   // S1: packed factors, or (gather mode) the pair's blocks sieved out of the
   // per-orbital pair-extended blocks into the slab
@@ -91,7 +98,7 @@ __device__ bool pair_forward(const FwdParams& prm, const PairDesc& pd, double* w
   // S3: F_i <- At^f_i - Ct_i J_f ;  V = F_i Ct_j^T + Ct_i At^f_j^T
   double* Fi = F;
   double* Fj = F + (int64_t)k * ld;
-  cta_gemm<TC, false, false>(k, m, m, Ci, ld, Jf, m, Fi, ld, -1.0, true, gs);
+  cta_gemm<TC, false, false>(k, m, m, Ci, ld, Jf_use, ld_jf, Fi, ld, -1.0, true, gs);
   double* V = prm.V + pd.off_kk;
   for (int r0 = 0; r0 < k; r0 += kTile)
     for (int c0 = 0; c0 < k; c0 += kTile) {
@@ -177,8 +184,15 @@ __device__ bool pair_forward_tc(const FwdParams& prm, const PairDesc& pd, double
   const double* Jf = prm.Jf + pd.off_mm;
   const double* Q = prm.Q + pd.off_pk;
   const double* T = prm.T + pd.off_kk;
-  for (int r = tid >> 5; r < m; r += kThreads / 32)
-    for (int c = tid & 31; c < m; c += 32) M[(int64_t)r * ld + c] = Jg[(int64_t)r * m + c];
+  load_metric(Jg, m, prm.metric_packed, M, ld);
+  const double* Jf_use = Jf;
+  int64_t ld_jf = m;
+  if (prm.metric_packed) {
+    double* W = ws + fwd_jf_off(p, k, m, prm.gdesc != nullptr);
+    unpack_metric(Jf, m, W, ld);
+    Jf_use = W;
+    ld_jf = ld;
+  }
   const double* Asrc[4] = {prm.Agi + pd.off_pm, prm.Agj + pd.off_pm, prm.Afi + pd.off_pm,
                            prm.Afj + pd.off_pm};
   if (prm.gdesc) {
@@ -214,7 +228,7 @@ __device__ bool pair_forward_tc(const FwdParams& prm, const PairDesc& pd, double
   double* Fi = F;
   double* Fj = F + (int64_t)k * ld;
   // F_i <- At^f_i - Ct_i J_f, computed as (J_f Ct_i^T)^T with J_f symmetric
-  if (!tc::gemm<false, false>(m, k, m, Jf, m, Ci, ld, Fi, ld, -1.0, true, st, ctrl, s_flag))
+  if (!tc::gemm<false, false>(m, k, m, Jf_use, ld_jf, Ci, ld, Fi, ld, -1.0, true, st, ctrl, s_flag))
     return false;
   double* V = prm.V + pd.off_kk;
   for (int r0 = 0; r0 < k; r0 += kTile)
@@ -410,11 +424,15 @@ cudaError_t launch_energy_total(const double* e_pair, const int32_t* status, int
 }
 
 // Streamed inputs, before the autotuner's sample launches (whose pairs come
-// from every group): one thread waits for the last group, which arrives last.
+// from every group): one thread waits for every group's flag in turn.
 __global__ void wait_ready_kernel(const uint32_t* ready, int32_t n_groups, uint32_t epoch,
                                   uint64_t timeout_ns, int32_t* err) {
-  if (threadIdx.x == 0 && n_groups > 0 && !wait_ready(ready, n_groups - 1, epoch, timeout_ns))
-    atomicExch(err, 1);
+  if (threadIdx.x != 0) return;
+  for (int32_t g = 0; g < n_groups; ++g)
+    if (!wait_ready(ready, g, epoch, timeout_ns)) {
+      atomicExch(err, 1);
+      return;
+    }
 }
 
 cudaError_t launch_wait_ready(const uint32_t* ready, int32_t n_groups, uint32_t epoch,

@@ -64,6 +64,9 @@ struct FwdParams {
   const int32_t* slot_group;
   uint32_t epoch;
   uint64_t arrival_timeout_ns;
+  // 1: J_g and J_f blocks are packed lower triangles (row r holds J[r][0..r]
+  // at r (r + 1) / 2); J_f is unpacked into the slab before its product
+  int32_t metric_packed;
 };
 
 struct BwdParams {
@@ -74,27 +77,36 @@ struct BwdParams {
 
 // per-CTA workspace (doubles) for a pair of sizes (p, k, m), forward / backward
 inline int64_t ld_of(int m) { return (int64_t)((m + 3) / 4 * 4); }
-inline int64_t fwd_ws(int p, int k, int m, bool gather = false) {
-  int64_t ld = ld_of(m);
-  return (int64_t)(m + 2 * k) * ld + 2 * (int64_t)k * ld + 64 +
-         (gather ? 4 * (int64_t)p * m + 64 : 0);
-}
 // offset of the sieved A blocks (4 x p x m) inside a forward slab
 inline __host__ __device__ int64_t fwd_sieve_off(int k, int m) {
   const int64_t ld = (m + 3) / 4 * 4;
   return ((int64_t)(m + 2 * k) * ld + 2 * (int64_t)k * ld + 31) / 32 * 32;
 }
-inline int64_t bwd_ws(int p, int k, int m, bool gather = false) {
+// offset of the unpacked J_f (m x ld) inside a forward slab (packed metrics)
+inline __host__ __device__ int64_t fwd_jf_off(int p, int k, int m, bool gather) {
+  return fwd_sieve_off(k, m) + (gather ? (4 * (int64_t)p * m + 64 + 31) / 32 * 32 : 0);
+}
+inline int64_t fwd_ws(int p, int k, int m, bool gather = false, bool packed = false) {
   int64_t ld = ld_of(m);
-  int64_t ldk = (k + 3) / 4 * 4;
-  // M = [J_g -> L; Ct_i; Ct_j] (m + 2k rows), F (2k rows: At^f, then H),
-  // R (2k rows: At^f - Ct J_f, then Z^T), G_V and V (k x k each)
-  return (int64_t)(m + 6 * k) * ld + 2 * (int64_t)k * ldk + 64 +
+  if (packed) return fwd_jf_off(p, k, m, gather) + (int64_t)m * ld + 64;
+  return (int64_t)(m + 2 * k) * ld + 2 * (int64_t)k * ld + 64 +
          (gather ? 4 * (int64_t)p * m + 64 : 0);
 }
 inline __host__ __device__ int64_t bwd_sieve_off(int k, int m) {
   const int64_t ld = (m + 3) / 4 * 4, ldk = (k + 3) / 4 * 4;
   return ((int64_t)(m + 6 * k) * ld + 2 * (int64_t)k * ldk + 31) / 32 * 32;
+}
+inline __host__ __device__ int64_t bwd_jf_off(int p, int k, int m, bool gather) {
+  return bwd_sieve_off(k, m) + (gather ? (4 * (int64_t)p * m + 64 + 31) / 32 * 32 : 0);
+}
+inline int64_t bwd_ws(int p, int k, int m, bool gather = false, bool packed = false) {
+  int64_t ld = ld_of(m);
+  int64_t ldk = (k + 3) / 4 * 4;
+  if (packed) return bwd_jf_off(p, k, m, gather) + (int64_t)m * ld + 64;
+  // M = [J_g -> L; Ct_i; Ct_j] (m + 2k rows), F (2k rows: At^f, then H),
+  // R (2k rows: At^f - Ct J_f, then Z^T), G_V and V (k x k each)
+  return (int64_t)(m + 6 * k) * ld + 2 * (int64_t)k * ldk + 64 +
+         (gather ? 4 * (int64_t)p * m + 64 : 0);
 }
 
 constexpr int kFwdVariants = 3;
@@ -103,8 +115,8 @@ cudaError_t launch_forward(const FwdParams& prm, int precision, int variant, int
 constexpr int kBwdVariants = 2;
 cudaError_t launch_backward(const BwdParams& prm, int precision, int variant, int n_ctas,
                             cudaStream_t s);
-// One warp waits (bounded) until every ready[g], g < n_groups, has reached
-// epoch; sets *err on expiry.
+// One thread waits (bounded, per flag) until every ready[g], g < n_groups,
+// has reached epoch; sets *err on expiry.
 cudaError_t launch_wait_ready(const uint32_t* ready, int32_t n_groups, uint32_t epoch,
                               uint64_t timeout_ns, int32_t* err, cudaStream_t s);
 cudaError_t launch_energy_total(const double* e_pair, const int32_t* status, int64_t n_pairs,

@@ -5,4 +5,4 @@ Gaussians, SPD metrics X X^T + 0.1 I from integer X, QR-orthonormalised PNO
 coefficients, pair lists and the packed ragged layout.
 """
 from .workloads import (Workload, WORKLOADS, tiny, c40h81, c160h321, lattice_quartet, custom,
-                        pair_inputs, packed_inputs, packed_offsets, unpack, ALIGN)
+                        pair_inputs, packed_inputs, packed_offsets, pack_lower, unpack, ALIGN)

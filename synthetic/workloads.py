@@ -352,18 +352,19 @@ def _round_up(x, a=ALIGN):
     return (x + a - 1) // a * a
 
 
-def packed_offsets(wl):
+def packed_offsets(wl, metric_packed=False):
     """Element offsets of each pair's blocks in the packed buffers.
 
     Returns dict with off_pm, off_mm, off_pk, off_kk (int64, n_pairs) and the
     buffer lengths len_pm, len_mm, len_pk, len_kk.  Blocks start on multiples of
-    ALIGN doubles."""
+    ALIGN doubles.  metric_packed: J blocks hold lower triangles, m (m + 1) / 2."""
     p = wl.n_pao.astype(np.int64)
     k = wl.n_pno.astype(np.int64)
     m = wl.n_aux.astype(np.int64)
     r, v = wl.n_rows, wl.n_virt       # factor rows and virtual dimension (augmented)
+    mm = m * (m + 1) // 2 if metric_packed else m * m
     out = {}
-    for name, sz in (("pm", r * m), ("mm", m * m), ("pk", p * k), ("kk", v * v)):
+    for name, sz in (("pm", r * m), ("mm", mm), ("pk", p * k), ("kk", v * v)):
         padded = _round_up(sz)
         off = np.zeros(len(sz), np.int64)
         if len(sz) > 1:
@@ -373,9 +374,15 @@ def packed_offsets(wl):
     return out
 
 
-def packed_inputs(wl, with_metrics=True):
-    """Host packed buffers (float64) of every pair, plus the offsets."""
-    lay = packed_offsets(wl)
+def pack_lower(J):
+    """Lower triangle of a square matrix, row by row (row r: J[r, 0..r])."""
+    return J[np.tril_indices(J.shape[0])]
+
+
+def packed_inputs(wl, with_metrics=True, metric_packed=False):
+    """Host packed buffers (float64) of every pair, plus the offsets.
+    metric_packed: J blocks stored as lower triangles (pack_lower)."""
+    lay = packed_offsets(wl, metric_packed)
     buf = {n: np.zeros(lay["len_pm"]) for n in ("Agi", "Agj", "Afi", "Afj")}
     if with_metrics:
         buf["Jg"] = np.zeros(lay["len_mm"])
@@ -390,7 +397,8 @@ def packed_inputs(wl, with_metrics=True):
         if with_metrics:
             for n in ("Jg", "Jf"):
                 o = lay["off_mm"][P]
-                buf[n][o:o + t[n].size] = t[n].ravel()
+                v = pack_lower(t[n]) if metric_packed else t[n].ravel()
+                buf[n][o:o + v.size] = v
         o = lay["off_pk"][P]
         buf["Q"][o:o + t["Q"].size] = t["Q"].ravel()
         o = lay["off_kk"][P]

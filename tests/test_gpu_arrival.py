@@ -3,8 +3,9 @@ whose CTAs wait for each group's arrival flag while the host-to-device copies
 of later groups are still running.
 
 - Results equal the resident path bit for bit (each pair's arithmetic does not
-  depend on the queue order; the total is summed in list order), on two calls
-  in a row with different data, so stale device buffers would show.
+  depend on the queue order; the total is summed in list order), on three
+  calls in a row with different data, so stale device buffers would show; with
+  groups spread over three copy streams they may also land out of order.
 - A flag that nothing writes makes the bounded wait expire: status 3 and
   PF12_ERR_TIMEOUT, and the context works again after a new upload.
 """
@@ -42,8 +43,9 @@ def _lists():
     return a, b
 
 
-@pytest.mark.parametrize("precision,variant", [("fp64", 1), ("mixed_fp32", None), ("mixed_fp32", 2)])
-def test_streamed_equals_resident(built, precision, variant):
+@pytest.mark.parametrize("precision,variant,streams", [("fp64", 1, 1), ("mixed_fp32", None, 1),
+                                                       ("mixed_fp32", 2, 1), ("fp64", 0, 3)])
+def test_streamed_equals_resident(built, precision, variant, streams):
     import paper_2008_03237_gb300 as pf
     from paper_2008_03237_gb300.stream import HostStreamer, arrival_groups
     wla, wlb = _lists()
@@ -51,7 +53,7 @@ def test_streamed_equals_resident(built, precision, variant):
         S.pair_inputs(wla, 3)["Agi"], S.pair_inputs(wlb, 3)["Agi"])
     eng = pf.PairF12(precision, variant=variant)
     # small groups: many waits inside one launch
-    hs = HostStreamer(eng, first_bytes=0.5e6, max_group_bytes=3e6)
+    hs = HostStreamer(eng, first_bytes=0.5e6, max_group_bytes=3e6, copy_streams=streams)
     ends = arrival_groups(wla.n_pao, wla.n_pno, wla.n_aux, 0.5e6, 3e6)
     assert len(ends) >= 8
     for wl in (wla, wlb, wla):

@@ -45,3 +45,23 @@ def test_arrival_groups_cover_the_list_and_grow():
     assert arrival_groups([], [], [], 1e9, 4e9).size == 0
     one = arrival_groups(wl.n_pao[:1], wl.n_pno[:1], wl.n_aux[:1], 1.0, 1.0)
     assert list(one) == [1]
+
+
+def test_packed_metric_layout():
+    """Metrics as packed lower triangles: block sizes m (m + 1) / 2 and row r of
+    the triangle at r (r + 1) / 2."""
+    wl = S.custom(3, 1, None, (5, 9), ("uniform", 2, 4), (4, 11))
+    full, lay_f = S.packed_inputs(wl)
+    tri, lay_t = S.packed_inputs(wl, metric_packed=True)
+    for P in range(wl.n_pairs):
+        m = int(wl.n_aux[P])
+        J = S.unpack(full["Jg"], lay_f["off_mm"], P, m, m)
+        o = int(lay_t["off_mm"][P])
+        for r in range(m):
+            row = tri["Jg"][o + r * (r + 1) // 2: o + r * (r + 1) // 2 + r + 1]
+            assert np.array_equal(row, J[r, :r + 1])
+        assert lay_t["off_mm"][P] % 32 == 0
+    m = wl.n_aux.astype(np.int64)
+    assert lay_t["len_mm"] == int(((m * (m + 1) // 2 + 31) // 32 * 32).sum())
+    for key in ("off_pm", "off_pk", "off_kk"):
+        assert np.array_equal(lay_t[key], lay_f[key])
