@@ -204,6 +204,24 @@ print(json.dumps(res))
 """
 
 
+def cpu_model():
+    """Host CPU model name (lscpu, else /proc/cpuinfo), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def cpu_oracle_rate(wl, budget_s, threads=None, steps=1):
     """FP64 CPU oracle (as it stands) on a deterministic sample of wl's pairs,
     parallel over pairs: `threads` worker processes with one BLAS thread each
@@ -575,6 +593,7 @@ def main():
     if not args.no_cpu and world == 1:
         (rate,), cores, sample = cpu_oracle_rate(wl, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                                "cpu_model": cpu_model(),
                                 "sample": sample}
         (rate1,), _, sample1 = cpu_oracle_rate(wl, max(3.0, args.cpu_seconds / 3), threads=1)
         line["cpu_baseline_1thread"] = {"value": rate1, "unit": "pairs/s", "cores": 1,
@@ -656,6 +675,7 @@ def run_reference(args, rank, world):
             "data": "synthetic (seeded Philox4x32-10 draws)", "impl": "reference",
             "config": {"workload": wl.name, "pairs": wl.n_pairs, "precision": "fp64"},
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(),
                              "sample": sample},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
