@@ -269,90 +269,110 @@ __device__ __forceinline__ bool chol_augmented(double* M, int64_t ld, int m, int
 }
 
 // ---------------------------------------------------------------------------
-// Backward solve Y <- Y L^{-1} (FP64) for nrows rows of Y (leading dimension
-// ldy) and the lower-triangular m x m factor L (leading dimension ld):
-// column blocks from the right, each a small in-register triangular solve
-// followed by a rank-nb update of the columns to its left.
-__device__ __forceinline__ void solve_right_lower(const double* L, int64_t ld, int m, double* Y,
-                                                  int64_t ldy, int nrows, CholSmem& cs,
-                                                  GemmSmem& gs) {
-  const int tid = threadIdx.x;
-  const int nblk = (m + kNB - 1) / kNB;
-  for (int cb = nblk - 1; cb >= 0; --cb) {
-    const int c0 = cb * kNB, nb = min(kNB, m - c0);
-    for (int e = tid; e < nb * nb; e += kThreads) {
-      const int r = e / nb, c = e - r * nb;
-      cs.d[r][c] = (c <= r) ? L[(int64_t)(c0 + r) * ld + c0 + c] : 0.0;
-    }
-    __syncthreads();
-    if (tid < nb) cs.inv[tid] = 1.0 / cs.d[tid][tid];
-    __syncthreads();
-    for (int r = tid; r < nrows; r += kThreads) {
-      double* row = Y + (int64_t)r * ldy + c0;
-      double x[kNB];
-#pragma unroll
-      for (int t = 0; t < kNB; ++t) x[t] = (t < nb) ? row[t] : 0.0;
-#pragma unroll
-      for (int t = kNB - 1; t >= 0; --t) {
-        if (t < nb) {
-          double s = x[t];
-#pragma unroll
-          for (int q = t + 1; q < kNB; ++q)
-            if (q < nb) s = fma(-x[q], cs.d[q][t], s);
-          x[t] = s * cs.inv[t];
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < kNB; ++t)
-        if (t < nb) row[t] = x[t];
-    }
-    __syncthreads();
-    if (c0 > 0)
-      cta_gemm<double, false, false>(nrows, c0, nb, Y + c0, ldy, L + (int64_t)c0 * ld, ld, Y, ldy,
-                                     -1.0, true, gs);
-  }
-}
+// Triangular solves with the Cholesky factor for nrows rows of Y (leading
+// dimension ldy; L is m x m lower triangular, leading dimension ld, only its
+// lower triangle is read).  Columns go in blocks of kNB, grouped kSolveGroup
+// blocks at a time as in the factorisation: inside a group every block first
+// takes a left-looking update from the group's solved blocks (depth < 256),
+// then a small in-register triangular solve (one thread per row); after the
+// group one deep update of depth up to 256 carries it to the remaining
+// columns, so Y is read and written once per group instead of once per block.
+constexpr int kSolveGroup = 8;
 
-// ---------------------------------------------------------------------------
-// Forward solve Y <- Y L^{-T} (FP64) for nrows rows of Y: column blocks from the
-// left, each an in-register triangular solve followed by a rank-nb update of
-// the columns to its right.
-__device__ __forceinline__ void solve_right_lowerT(const double* L, int64_t ld, int m, double* Y,
-                                                   int64_t ldy, int nrows, CholSmem& cs,
-                                                   GemmSmem& gs) {
+// In-register solve of the nb-column block at c0 of every row, with the
+// block's diagonal block of L staged in cs; forward (lower, L^T on the right)
+// or backward (L on the right) order.
+template <bool kForward>
+__device__ __forceinline__ void solve_block(const double* L, int64_t ld, double* Y, int64_t ldy,
+                                            int nrows, int c0, int nb, CholSmem& cs) {
   const int tid = threadIdx.x;
-  for (int kb = 0; kb < m; kb += kNB) {
-    const int nb = min(kNB, m - kb);
-    for (int e = tid; e < nb * nb; e += kThreads) {
-      const int r = e / nb, c = e - r * nb;
-      cs.d[r][c] = (c <= r) ? L[(int64_t)(kb + r) * ld + kb + c] : 0.0;
-    }
-    __syncthreads();
-    if (tid < nb) cs.inv[tid] = 1.0 / cs.d[tid][tid];
-    __syncthreads();
-    for (int r = tid; r < nrows; r += kThreads) {
-      double* row = Y + (int64_t)r * ldy + kb;
-      double x[kNB];
+  for (int e = tid; e < nb * nb; e += kThreads) {
+    const int r = e / nb, c = e - r * nb;
+    cs.d[r][c] = (c <= r) ? L[(int64_t)(c0 + r) * ld + c0 + c] : 0.0;
+  }
+  __syncthreads();
+  if (tid < nb) cs.inv[tid] = 1.0 / cs.d[tid][tid];
+  __syncthreads();
+  for (int r = tid; r < nrows; r += kThreads) {
+    double* row = Y + (int64_t)r * ldy + c0;
+    double x[kNB];
 #pragma unroll
-      for (int t = 0; t < kNB; ++t) x[t] = (t < nb) ? row[t] : 0.0;
+    for (int t = 0; t < kNB; ++t) x[t] = (t < nb) ? row[t] : 0.0;
+    if (kForward) {
 #pragma unroll
       for (int t = 0; t < kNB; ++t) {
         if (t < nb) {
-          double s = x[t];
+          double sum = x[t];
 #pragma unroll
-          for (int q = 0; q < t; ++q) s = fma(-x[q], cs.d[t][q], s);
-          x[t] = s * cs.inv[t];
+          for (int q = 0; q < t; ++q) sum = fma(-x[q], cs.d[t][q], sum);
+          x[t] = sum * cs.inv[t];
         }
       }
+    } else {
 #pragma unroll
-      for (int t = 0; t < kNB; ++t)
-        if (t < nb) row[t] = x[t];
+      for (int t = kNB - 1; t >= 0; --t) {
+        if (t < nb) {
+          double sum = x[t];
+#pragma unroll
+          for (int q = t + 1; q < kNB; ++q)
+            if (q < nb) sum = fma(-x[q], cs.d[q][t], sum);
+          x[t] = sum * cs.inv[t];
+        }
+      }
     }
-    __syncthreads();
-    if (kb + nb < m)
-      cta_gemm<double, false, true>(nrows, m - kb - nb, nb, Y + kb, ldy,
-                                    L + (int64_t)(kb + nb) * ld + kb, ld, Y + kb + nb, ldy, -1.0,
-                                    true, gs);
+#pragma unroll
+    for (int t = 0; t < kNB; ++t)
+      if (t < nb) row[t] = x[t];
+  }
+  __syncthreads();
+}
+
+// Backward solve Y <- Y L^{-1}: column blocks from the right.
+__device__ __forceinline__ void solve_right_lower(const double* L, int64_t ld, int m, double* Y,
+                                                  int64_t ldy, int nrows, CholSmem& cs,
+                                                  GemmSmem& gs) {
+  const int nblk = (m + kNB - 1) / kNB;
+  for (int gb_hi = nblk; gb_hi > 0;) {
+    const int gb_lo = max(0, gb_hi - kSolveGroup);
+    const int g0 = gb_lo * kNB, g1 = min(m, gb_hi * kNB);
+    for (int cb = gb_hi - 1; cb >= gb_lo; --cb) {
+      const int c0 = cb * kNB, nb = min(kNB, m - c0), cend = c0 + nb;
+      if (cend < g1) {   // Y_blk -= X[:, cend:g1] L[cend:g1, blk]
+        cta_gemm<double, false, false>(nrows, nb, g1 - cend, Y + cend, ldy,
+                                       L + (int64_t)cend * ld + c0, ld, Y + c0, ldy, -1.0, true, gs);
+        __syncthreads();
+      }
+      solve_block<false>(L, ld, Y, ldy, nrows, c0, nb, cs);
+    }
+    if (g0 > 0) {        // Y[:, 0:g0] -= X[:, g0:g1] L[g0:g1, 0:g0]
+      cta_gemm<double, false, false>(nrows, g0, g1 - g0, Y + g0, ldy, L + (int64_t)g0 * ld, ld, Y,
+                                     ldy, -1.0, true, gs);
+      __syncthreads();
+    }
+    gb_hi = gb_lo;
+  }
+}
+
+// Forward solve Y <- Y L^{-T}: column blocks from the left.
+__device__ __forceinline__ void solve_right_lowerT(const double* L, int64_t ld, int m, double* Y,
+                                                   int64_t ldy, int nrows, CholSmem& cs,
+                                                   GemmSmem& gs) {
+  for (int g0 = 0; g0 < m; g0 += kSolveGroup * kNB) {
+    const int g1 = min(m, g0 + kSolveGroup * kNB);
+    for (int kb = g0; kb < g1; kb += kNB) {
+      const int nb = min(kNB, m - kb);
+      if (kb > g0) {     // Y_blk -= X[:, g0:kb] L[blk, g0:kb]^T
+        cta_gemm<double, false, true>(nrows, nb, kb - g0, Y + g0, ldy, L + (int64_t)kb * ld + g0,
+                                      ld, Y + kb, ldy, -1.0, true, gs);
+        __syncthreads();
+      }
+      solve_block<true>(L, ld, Y, ldy, nrows, kb, nb, cs);
+    }
+    if (g1 < m) {        // Y[:, g1:m] -= X[:, g0:g1] L[g1:m, g0:g1]^T
+      cta_gemm<double, false, true>(nrows, m - g1, g1 - g0, Y + g0, ldy, L + (int64_t)g1 * ld + g0,
+                                    ld, Y + g1, ldy, -1.0, true, gs);
+      __syncthreads();
+    }
   }
 }
 
