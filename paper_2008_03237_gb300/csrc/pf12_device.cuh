@@ -27,6 +27,43 @@ struct __align__(16) CholSmem {
 // for r0 <= r < min(r0 + 64, M), c0 <= c < min(c0 + 64, N), where
 //   A(r, t) = TA ? A[t * lda + r] : A[r * lda + t]
 //   B(t, c) = TB ? B[c * ldb + t] : B[t * ldb + c].
+// FP64 <-> FP32 conversions in integer arithmetic.  On this part the FP64 pipe
+// is the bottleneck and executes the hardware conversions too; these run on
+// the integer pipes instead.  Binary64 -> binary32 rounds to nearest, ties to
+// even: keep 23 of the 52 fraction bits, rebias the exponent (1023 -> 127) and
+// add one unit when the 29 dropped bits exceed half a unit, or equal it with
+// an odd kept fraction (a carry into the exponent is the correct result,
+// including the step to infinity).  Values whose result is not a normal
+// binary32 (zero, subnormal, infinity, NaN) take the hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rne(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned int hi = static_cast<unsigned int>(b >> 32), lo = static_cast<unsigned int>(b);
+  const unsigned int e = (hi >> 20) & 0x7ffu;
+  if (e < 1023u - 126u || e > 1023u + 127u) return __double2float_rn(x);
+  unsigned int r = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned int rest = lo & 0x1fffffffu;
+  r += (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ? 1u : 0u;
+  return __uint_as_float(r);
+}
+
+// Binary32 -> binary64, exact: rebias the exponent (127 -> 1023) and widen the
+// fraction; zero, subnormal, infinity and NaN take the hardware conversion.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return static_cast<double>(f);
+  const unsigned long long b = (static_cast<unsigned long long>(u & 0x80000000u) << 32) |
+                               (static_cast<unsigned long long>(e + 896u) << 52) |
+                               (static_cast<unsigned long long>(u & 0x7fffffu) << 29);
+  return __longlong_as_double(static_cast<long long>(b));
+}
+
+template <typename TC>
+__device__ __forceinline__ TC to_operand(double x) {
+  if constexpr (sizeof(TC) == sizeof(float)) return f64_to_f32_rne(x);
+  else return x;
+}
+
 // The 64 x 64 tile is split into 32 blocks of 8 x 16.  A block is active when
 // it meets [0, M) x [0, N) and, if tri_rows > 0, is not entirely above the
 // diagonal within the first tri_rows rows.  Active blocks are dealt
@@ -86,7 +123,7 @@ __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double*
       else     { r = tid & 63; t = (tid >> 6) + 4 * s; }
       const int gr = r0 + r, gt = k0 + t;
       TC v = TC(0);
-      if (gr < M && gt < K) v = (TC)(TA ? A[(int64_t)gt * lda + gr] : A[(int64_t)gr * lda + gt]);
+      if (gr < M && gt < K) v = to_operand<TC>(TA ? A[(int64_t)gt * lda + gr] : A[(int64_t)gr * lda + gt]);
       as[t][r] = v;
     }
 #pragma unroll
@@ -96,7 +133,7 @@ __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double*
       else    { c = tid & 63; t = (tid >> 6) + 4 * s; }
       const int gc = c0 + c, gt = k0 + t;
       TC v = TC(0);
-      if (gc < N && gt < K) v = (TC)(TB ? B[(int64_t)gc * ldb + gt] : B[(int64_t)gt * ldb + gc]);
+      if (gc < N && gt < K) v = to_operand<TC>(TB ? B[(int64_t)gc * ldb + gt] : B[(int64_t)gt * ldb + gc]);
       bs[t][c] = v;
     }
     __syncthreads();
@@ -137,7 +174,7 @@ __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double*
             for (int i = 0; i < 2; ++i)
 #pragma unroll
               for (int j = 0; j < 2; ++j) {
-                if (orow[q] >= 0) accd[q][i][j] += (double)accf[q][i][j];
+                if (orow[q] >= 0) accd[q][i][j] += f32_to_f64(accf[q][i][j]);
                 accf[q][i][j] = 0.0f;
               }
         }
