@@ -86,7 +86,7 @@ def make_workload(name, max_pairs, rank=0):
 # DRAM bytes (read + write) of one launch of the SIMT 3-CTAs/SM forward kernel,
 # measured by ncu on a 1,368-pair subset of the C160H321 chain (16.9 GB of
 # algorithmic input bytes); scaled to other lists by algorithmic input bytes.
-TRAFFIC_CAPTURE = {"bytes": 92.204048e9, "alg_bytes": 16898189704.0, "variant": 1,
+TRAFFIC_CAPTURE = {"bytes": 85.735969e9, "alg_bytes": 16898189704.0, "variant": 1,
                    "precision": "mixed_fp32"}
 
 
