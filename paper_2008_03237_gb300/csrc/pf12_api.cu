@@ -102,6 +102,8 @@ struct pf12_ctx {
   bool fixed_allocated = false;
   std::string prev_key;      // tuning key of the previous upload (variant kept if equal)
   int prev_variant = -1;
+  std::string prev_bwd_key;  // the same for the adjoint's variant
+  int prev_bwd_variant = -1;
 
   // timers
   cudaEvent_t ev[6] = {};
@@ -135,6 +137,10 @@ void free_pairs(pf12_ctx* c) {
   if (c->variant >= 0) {
     c->prev_key = c->tune_key;
     c->prev_variant = c->variant;
+  }
+  if (c->bwd_variant >= 0) {
+    c->prev_bwd_key = c->tune_key;
+    c->prev_bwd_variant = c->bwd_variant;
   }
   c->variant = -1;
   c->bwd_variant = -1;
@@ -492,6 +498,9 @@ static int upload_impl(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n
     c->variant = c->prev_variant;     // same size signature as the last list: keep its tuning
     c->n_ctas = c->n_ctas_v[c->variant];
   }
+  if (c->prev_bwd_variant >= 0 && c->prev_bwd_key == c->tune_key &&
+      c->n_ctas_bwd_v[c->prev_bwd_variant] > 0)
+    c->bwd_variant = c->prev_bwd_variant;
 
   const size_t n = (size_t)std::max<int64_t>(n_pairs, 1);
   cudaError_t e = cudaSuccess;
@@ -882,10 +891,26 @@ namespace {
 
 // Adjoint tuner: like the forward tuner, on the same cost-spread sample (the
 // sample's gradient blocks are overwritten by the real launch that follows).
+// The choice is kept across uploads with the same size signature and cached
+// in the tuner_cache file under the forward key plus "|bwd"; without that, a
+// streamed run re-timed the adjoint on every batch (C-quartet lattice: 140 s
+// per forward + adjoint step instead of about 90 s).
 int tune_backward(pf12_ctx* c, pf12::BwdParams b) {
   if (c->n_pairs <= c->n_ctas_bwd_v[0] || c->n_sample == 0) {
     c->bwd_variant = 0;
     return PF12_OK;
+  }
+  const std::string key = c->tune_key + "|bwd";
+  if (!c->tuner_cache.empty()) {     // same file as the forward tuner, own key
+    FILE* f = fopen(c->tuner_cache.c_str(), "r");
+    if (f) {
+      char k[512];
+      int v = -1;
+      while (fscanf(f, "%511s %d %*f %*f %*f", k, &v) == 2)
+        if (key == k && v >= 0 && v < pf12::kBwdVariants && c->n_ctas_bwd_v[v] > 0) c->bwd_variant = v;
+      fclose(f);
+    }
+    if (c->bwd_variant >= 0) return PF12_OK;
   }
   b.f.desc = c->d_desc_sample;
   int best = 0;
@@ -905,6 +930,13 @@ int tune_backward(pf12_ctx* c, pf12::BwdParams b) {
     if (ms < c->tune_bwd_ms[best]) best = v;
   }
   c->bwd_variant = best;
+  if (!c->tuner_cache.empty()) {
+    FILE* fo = fopen(c->tuner_cache.c_str(), "a");
+    if (fo) {
+      fprintf(fo, "%s %d %.3f %.3f 0\n", key.c_str(), best, c->tune_bwd_ms[0], c->tune_bwd_ms[1]);
+      fclose(fo);
+    }
+  }
   return PF12_OK;
 }
 
