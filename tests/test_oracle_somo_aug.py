@@ -122,3 +122,17 @@ def test_augmented_gradient_central_differences(P):
             an = float(np.sum(g[name] * dvec))
             scale = max(abs(an), np.linalg.norm(g[name]) * 1e-3)
             assert abs(fd - an) <= 1e-7 * scale + 1e-12, (name, fd, an)
+
+
+def test_augmented_tiny_matches_stored_oracle_values():
+    """Stored by tests/golden/make_golden.py (oracle/ and synthetic/ only):
+    guards the augmented oracle and generator against silent drift."""
+    import json
+    import math
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tiny_aug_oracle.json")
+    with open(path) as fh:
+        ref = json.load(fh)
+    r = O.run(S.tiny().augmented())
+    assert np.allclose(r["e_pair"], np.array(ref["e_pair"]), rtol=1e-12, atol=1e-13)
+    assert math.isclose(r["E"], ref["E"], rel_tol=1e-12)
