@@ -19,6 +19,8 @@ cores (--impl reference times that oracle as the reference arm).
 Multi-GPU (torchrun): every rank runs an independent copy of the workload
 (its own seed), so per-GPU work is fixed (weak scaling) and there is no
 data-path collective; value = all ranks' pairs / the slowest rank's time.
+With --shard the ranks instead split one pair list (LPT shards) and gather the
+pair energies in list order every step (strong scaling).
 """
 import argparse
 import json
@@ -34,7 +36,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "F12 pairs/s & TFLOP/s, mixed-prec vs plain FP64 on 1 GB300 at ≤1 µEh error"
-FP64_PEAK_TFLOPS = 1.25     # nominal GB300 dense FP64 (DFMA), 152 SMs x 4 flop/clk x 2.07 GHz
+# FP64 peak of the pipe the fused kernels are bound by, derived from unit counts
+# and clock: 152 SMs x 2 DFMA/clk/SM (4 flop/clk) x 2.07 GHz maximum SM clock
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 
 
 def measured_peaks():
@@ -60,6 +64,11 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint figure (C40H81)")
+    ap.add_argument("--shard", action="store_true",
+                    help="torchrun: split ONE pair list over the ranks (LPT) and gather the pair "
+                         "energies in list order every step (strong scaling); default: every "
+                         "rank evaluates its own copy of the workload (weak scaling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--stream-gb", type=float, default=0.0,
                     help="pair-streamed run: inputs drawn on the device batch by batch "
@@ -70,6 +79,25 @@ def parse():
     ap.add_argument("--variant", type=int, default=None,
                     help="force a forward kernel variant instead of autotuning (profiling)")
     return ap.parse_args()
+
+
+def fp64_probe(iters=40000):
+    """Measured FP64 FMA rate of this GPU (libpf12probe.so, CUDA events), TFLOP/s."""
+    import ctypes
+    from paper_2008_03237_gb300 import build as b
+    lib = ctypes.CDLL(b.build_probe())
+    fn = lib.pf12probe_fp64_fma
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    tf, ms = ctypes.c_double(0), ctypes.c_double(0)
+    best = None
+    for _ in range(3):
+        rc = fn(iters, ctypes.byref(tf), ctypes.byref(ms))
+        if rc != 0:
+            return None
+        best = tf.value if best is None else max(best, tf.value)
+    return {"tflops": best, "kernel": "dfma_chains (16 independent FMA chains per thread, "
+            "8 CTAs x 256 threads per SM)", "ms_per_launch": ms.value, "best_of": 3}
 
 
 def make_workload(name, max_pairs, rank=0):
@@ -411,7 +439,45 @@ def run_ours(args, rank, world, local_rank):
         out["e2e"] = run_e2e(args, wl, t, lay, pf, torch)
     del t
     torch.cuda.empty_cache()
+    if not args.no_adjoint and world == 1:
+        out["adjoint"] = run_adjoint(args, pf, torch, device)
+    out["fp64_probe"] = fp64_probe()
     return wl, f64, fmix, byts, out
+
+
+def run_adjoint(args, pf, torch, device, name="c40h81"):
+    """Device time of the adjoint kernel (pf12_backward) on the C40H81 chain:
+    gradients with respect to A^g, A^f, Q and T of all 2,821 pairs into
+    resident buffers, three launches after the tuning one, CUDA events on the
+    launching stream.  Algorithmic FP64 work per pair: m^3/3 + 8 k m^2 (the
+    factorisation, the two solves of the forward fit and the two of
+    Z^T = R J_g^{-1})."""
+    wl = make_workload(name, 0)
+    t, lay = device.allocate(wl)
+    device.fill(wl, t, lay)
+    eng = pf.PairF12(args.precision)
+    eng.upload_pairs(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
+    eng.fit()
+    eng.energy(want_host=False)
+    grads = {x: torch.zeros_like(t[x]) for x in ("Agi", "Agj", "Afi", "Afj", "Q", "T")}
+    eng.backward(1.0, grads)
+    ms = []
+    for _ in range(3):
+        eng.backward(1.0, grads)
+        ms.append(eng.stats()["ms_backward"])
+    st = eng.stats()
+    bad = int((eng.pair_status() != 0).sum())
+    eng.close()
+    del grads, t
+    torch.cuda.empty_cache()
+    k, m = wl.n_pno.astype(float), wl.n_aux.astype(float)
+    f64_b = float((m ** 3 / 3 + 8 * k * m * m).sum())
+    ms_mean = float(np.mean(ms))
+    return {"workload": wl.name, "pairs": wl.n_pairs, "precision": args.precision,
+            "kernel": "pair_backward_kernel (fused persistent adjoint)",
+            "ms_per_launch": ms_mean, "ms_launches": ms, "fp64_tflops": f64_b / ms_mean / 1e9,
+            "frac_of_fp64_peak": f64_b / ms_mean / 1e9 / FP64_PEAK_TFLOPS,
+            "variant": st["bwd_variant"], "tune_ms": st["tune_bwd_ms"], "pairs_failed": bad}
 
 
 class _Null:
@@ -530,6 +596,8 @@ def main():
         dist.init_process_group("nccl")
     if args.stream_gb:
         return run_streamed(args, rank, world, local_rank)
+    if args.shard and world > 1:
+        return run_sharded(args, rank, world, local_rank)
     wl, f64, fmix, byts, o = run_ours(args, rank, world, local_rank)
     ms = o["ms"]
     if world > 1:
@@ -544,6 +612,7 @@ def main():
     value = world * n_pairs / ms * 1e3
     flops_dom = f64 + (fmix if args.precision == "fp64" else 0.0)
     achieved = flops_dom / o["ms_fit"] / 1e9
+    probe = o.get("fp64_probe")
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -566,8 +635,11 @@ def main():
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": traffic_bytes(args, wl, byts, o["stats"]["tile_config"]),
                      "kernel": "pair_forward_kernel (fused persistent)",
-                     "peak_kind": "FP64 DFMA pipe, nominal 1.25 TFLOP/s (152 SMs x 4 flop/clk x 2.07 GHz)",
+                     "peak_kind": "FP64 DFMA pipe, derived: 152 SMs x 4 flop/clk x 2.07 GHz",
+                     "peak_measured": probe["tflops"] if probe else None,
+                     "frac_of_measured": achieved / probe["tflops"] if probe else None,
                      "ms_per_launch": o["ms_fit"]},
+        "fp64_probe": probe,
         "clocks": o["clocks"],
         "gpu_launches": 2 * args.steps,
         "E_total_raw": o["E"], "pairs_failed": o["status_bad"],
@@ -576,7 +648,7 @@ def main():
                       "sample_ms": o["stats"]["tune_ms"],
                       "ctas": o["stats"]["ctas_variant"]},
     }
-    for key in ("fp64_mode", "error_vs_fp64", "e2e"):
+    for key in ("fp64_mode", "error_vs_fp64", "e2e", "adjoint"):
         if key in o:
             line[key] = o[key]
     if args.backward:
@@ -598,6 +670,76 @@ def main():
         (rate1,), _, sample1 = cpu_oracle_rate(wl, max(3.0, args.cpu_seconds / 3), threads=1)
         line["cpu_baseline_1thread"] = {"value": rate1, "unit": "pairs/s", "cores": 1,
                                         "kind": "oracle", "sample": sample1}
+    print(json.dumps(line), flush=True)
+
+
+def run_sharded(args, rank, world, local_rank):
+    """One pair list split over the ranks: longest-processing-time shards by
+    the kernel's cost model, every rank holding and evaluating its shard only;
+    each step ends with the pair energies gathered over NCCL in pair-list
+    order and summed on the host (shard.gather_pair_energies).  value = the
+    list's pairs / the slowest rank's step time (strong scaling)."""
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    import paper_2008_03237_gb300 as pf
+    from paper_2008_03237_gb300.shard import gather_pair_energies, lpt_partition, pair_costs
+    from synthetic import device
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        __graft_entry__.build()
+    dist.barrier()
+    __graft_entry__.build()
+    wl = make_workload(args.workload, args.max_pairs)          # the same list on every rank
+    mine = lpt_partition(pair_costs(wl.n_pao, wl.n_pno, wl.n_aux), world)[rank]
+    sub = wl.subset(mine)
+    f64, fmix, byts = flops_bytes(wl)
+    t, lay = device.allocate(sub)
+    device.fill(sub, t, lay)
+    eng = pf.PairF12(args.precision, variant=args.variant)
+    eng.upload_pairs(sub.n_orb, sub.orb_kind, sub.pi, sub.pj, sub.n_pao, sub.n_pno, sub.n_aux, t, lay)
+    e_loc = torch.empty((sub.n_pairs, 3), dtype=torch.float64, device="cuda")
+
+    def step():
+        eng.fit()
+        eng.energy(e_pair=e_loc, want_host=False)
+        return gather_pair_energies(e_loc.cpu().numpy(), mine, wl.n_pairs)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with sampler:
+        ev0.record()
+        for _ in range(args.steps):
+            full, total = step()
+        ev1.record()
+        torch.cuda.synchronize()
+    dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    x = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    ms = float(x.item())
+    bad = int((eng.pair_status() != 0).sum())
+    eng.close()
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": wl.n_pairs / ms * 1e3, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f64+f32" if args.precision != "fp64" else "f64",
+            "data": "synthetic (seeded Philox4x32-10 draws, device-resident, each rank its shard)",
+            "config": {"workload": wl.name, "pairs": wl.n_pairs, "precision": args.precision,
+                       "sharding": "LPT over ranks, pair energies all-gathered in list order",
+                       "pairs_rank0": int(len(mine)),
+                       "l2": f"inputs {byts / 1e9:.0f} GB >> 129 MB L2, no flush"},
+            "tflops": {"fp64": f64 / ms / 1e9, "mixed_part": fmix / ms / 1e9},
+            "E_total_raw": total, "pairs_failed_rank0": bad, "clocks": sampler.summary(),
+            "gpu_launches": 2 * args.steps, "e2e": None}
     print(json.dumps(line), flush=True)
 
 

@@ -229,7 +229,8 @@ int pf12_energy(pf12_ctx* ctx, double* e_pair_dev, double* E_host);
  * amplitudes (J_g, J_f are constants).  Recomputes the forward intermediates
  * pair by pair instead of storing them.  Outputs use the input layouts
  * (off_pm / off_pk / off_kk) and are overwritten (not accumulated); any output
- * pointer may be NULL to skip it.  Formulas, with alpha, beta the weights of
+ * pointer may be NULL to skip it.  A pair whose J_g is not SPD gets status
+ * NOT_SPD (pf12_pair_status) and all-zero gradient blocks.  Formulas, with alpha, beta the weights of
  * E_P = alpha d + beta x:
  *   G_V = alpha T + beta T^T,   dT = alpha V + beta V^T
  *   dAf_i = Q G_V Ct_j,  dAf_j = Q G_V^T Ct_i
@@ -314,8 +315,12 @@ int pf12_backward_gather(pf12_ctx* ctx, double dE, double* dBg, double* dBf, dou
  *     number of concurrent pairs is whatever number of slabs fits (at most
  *     2 per SM), pairs are taken in the caller's order.
  *   Set-up: the first call on each device looks up the array's device
- *     address (cudaGetSymbolAddress) with that device current; make that
- *     first call before any stream capture.
+ *     address (cudaGetSymbolAddress) with that device current.
+ *   Not capturable: every call copies pair descriptors from host stack
+ *     memory, synchronises the stream and reads the total back, none of
+ *     which a stream capture can hold; on a capturing stream the call
+ *     returns PF12_ERR_UNSUPPORTED before any other CUDA call, so the
+ *     caller's capture stays valid.
  *   Sharing: every call uses the same array and leaves the last call's
  *     contents in it; calls whose GPU work overlaps (other streams or host
  *     threads) race on it and must be serialised by the caller.

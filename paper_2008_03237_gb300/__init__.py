@@ -244,34 +244,56 @@ class PairF12Energy(torch.autograd.Function):
 
     forward(ctx, Agi, Agj, Afi, Afj, Jg, Jf, Q, T, meta) with meta a dict of
     n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, off_pm, off_mm, off_pk,
-    off_kk and optionally precision.  backward recomputes V per pair in the
-    library's adjoint kernel."""
+    off_kk and optionally precision, variant and tuner_cache (PairF12's
+    options).  backward recomputes V per pair in the
+    library's adjoint kernel.
+
+    The library reads the inputs through raw device pointers, so forward saves
+    them with save_for_backward: their storage stays alive until backward, and
+    autograd raises if one of them is modified in place in between.  The
+    engine is released after the first backward; a second backward
+    (retain_graph=True) uploads the saved inputs into a new one."""
+
+    @staticmethod
+    def _engine(tensors, meta):
+        eng = PairF12(meta.get("precision", "fp64"), variant=meta.get("variant"),
+                      tuner_cache=meta.get("tuner_cache"))
+        eng.upload_pairs(meta["n_orb"], meta["orb_kind"], meta["pi"], meta["pj"], meta["n_pao"],
+                         meta["n_pno"], meta["n_aux"], tensors, meta)
+        return eng
 
     @staticmethod
     def forward(ctx, Agi, Agj, Afi, Afj, Jg, Jf, Q, T, meta):
-        eng = PairF12(meta.get("precision", "fp64"))
-        tensors = dict(zip(TENSOR_NAMES, (Agi, Agj, Afi, Afj, Jg, Jf, Q, T)))
-        eng.upload_pairs(meta["n_orb"], meta["orb_kind"], meta["pi"], meta["pj"], meta["n_pao"],
-                         meta["n_pno"], meta["n_aux"], tensors, meta)
+        inputs = (Agi, Agj, Afi, Afj, Jg, Jf, Q, T)
+        eng = PairF12Energy._engine(dict(zip(TENSOR_NAMES, inputs)), meta)
         eng.fit()
         E, _ = eng.energy()
-        ctx.eng = eng
-        ctx.shapes = [t.shape for t in (Agi, Agj, Afi, Afj, Q, T)]
+        ctx.meta = meta
+        if not any(ctx.needs_input_grad[:8]):   # no backward will come: release now
+            eng.close()
+            ctx.eng = None
+        else:
+            ctx.save_for_backward(*inputs)
+            ctx.eng = eng
         return torch.tensor(E, dtype=torch.float64, device=Agi.device)
 
     @staticmethod
     def backward(ctx, gE):
+        saved = ctx.saved_tensors          # raises if an input was modified in place
         eng = ctx.eng
+        if eng is None or getattr(eng, "_h", None) is None:
+            eng = PairF12Energy._engine(dict(zip(TENSOR_NAMES, saved)), ctx.meta)
         need = ctx.needs_input_grad
         names = ("Agi", "Agj", "Afi", "Afj", "Q", "T")
         idx = (0, 1, 2, 3, 6, 7)
         grads = {}
-        for n, i, shp in zip(names, idx, ctx.shapes):
+        for n, i in zip(names, idx):
             if need[i]:
-                grads[n] = torch.zeros(shp, dtype=torch.float64, device=gE.device)
+                grads[n] = torch.zeros_like(saved[i], memory_format=torch.contiguous_format)
         eng.backward(float(gE), grads)
         out = [grads.get(n) for n in names]
         eng.close()
+        ctx.eng = None
         return out[0], out[1], out[2], out[3], None, None, out[4], out[5], None
 
 

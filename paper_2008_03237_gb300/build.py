@@ -17,7 +17,11 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libpairf12.so")
-SOURCES = ["pf12_api.cu", "pf12_forward.cu", "pf12_backward.cu"]
+# host-side translation units, then one per kernel variant (csrc/inst/): the
+# variants are large fused kernels, and compiling them apart lets them build
+# in parallel
+SOURCES = ["pf12_api.cu", "pf12_forward.cu", "pf12_backward.cu"] + sorted(
+    os.path.join("inst", f) for f in os.listdir(os.path.join(CSRC, "inst")) if f.endswith(".cu"))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,7 +43,7 @@ def cuda_lib_dir():
 
 
 def _compile(src, extra):
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+    obj = os.path.join(BUILD, os.path.splitext(src)[0].replace(os.sep, "_") + ".o")
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
            "-I", os.path.join(ROOT, "include"), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -53,6 +57,7 @@ def needs_build():
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [
+        os.path.join(CSRC, "inst", f) for f in os.listdir(os.path.join(CSRC, "inst"))] + [
         os.path.join(ROOT, "include", "pairf12.h"), os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 
@@ -62,7 +67,7 @@ def build(verbose=False, ptxas_info=False, force=False):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     extra = ["-Xptxas", "-v"] if ptxas_info else []
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
+    with cf.ThreadPoolExecutor(min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
         results = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     objs = [o for o, _ in results]
     if verbose or ptxas_info:
@@ -78,6 +83,26 @@ def build(verbose=False, ptxas_info=False, force=False):
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
     return LIB
+
+
+PROBE_SRC = os.path.join(CSRC, "probe", "fp64_peak.cu")
+PROBE_LIB = os.path.join(PKG, "libpf12probe.so")
+
+
+def build_probe(force=False):
+    """libpf12probe.so: the FP64 FMA-pipe throughput probe the benchmark uses
+    as its roofline denominator (not part of the pair-F12 library)."""
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= max(
+            os.path.getmtime(PROBE_SRC), os.path.getmtime(os.path.abspath(__file__))):
+        return PROBE_LIB
+    tmp = PROBE_LIB + ".tmp"
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+           PROBE_SRC, "-o", tmp, "-cudart", "shared", "-Xlinker", "-rpath," + cuda_lib_dir()]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for the FP64 probe:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 if __name__ == "__main__":

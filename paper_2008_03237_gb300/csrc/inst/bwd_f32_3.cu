@@ -1,0 +1,19 @@
+// Adjoint pair kernel, FP32-class products, 3 CTAs per SM.
+// One kernel variant per translation unit, so that the variants compile in
+// parallel.
+#include "../pf12_backward.cuh"
+
+namespace pf12 {
+
+cudaError_t launch_bwd_f32_3(const BwdParams& prm, int n_ctas, cudaStream_t s) {
+  pair_backward_kernel<float, 3><<<n_ctas, kThreads, 0, s>>>(prm);
+  return cudaGetLastError();
+}
+
+int occupancy_bwd_f32_3() {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_backward_kernel<float, 3>, kThreads, 0);
+  return n;
+}
+
+}  // namespace pf12

@@ -1,0 +1,19 @@
+// Adjoint pair kernel, FP64 products, 2 CTAs per SM.
+// One kernel variant per translation unit, so that the variants compile in
+// parallel.
+#include "../pf12_backward.cuh"
+
+namespace pf12 {
+
+cudaError_t launch_bwd_f64_2(const BwdParams& prm, int n_ctas, cudaStream_t s) {
+  pair_backward_kernel<double, 2><<<n_ctas, kThreads, 0, s>>>(prm);
+  return cudaGetLastError();
+}
+
+int occupancy_bwd_f64_2() {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_backward_kernel<double, 2>, kThreads, 0);
+  return n;
+}
+
+}  // namespace pf12

@@ -1,8 +1,6 @@
-// Fused forward pair kernel: one persistent launch evaluates, for every pair,
-// the projections onto the PNOs, the FP64 Cholesky of J_g with the forward
-// solve riding along, the FP64 backward solve, the robust-fit V and the pair
-// energies.  Pairs are taken from a cost-sorted queue through one atomic
-// counter (no inter-CTA waits).
+// Host side of the fused forward pair kernel (device code: pf12_forward.cuh):
+// variant dispatch, the deterministic energy total, the arrival wait used
+// before tuning on streamed inputs, and the allocation-free entry point.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -12,367 +10,34 @@
 #include "../../include/pairf12.h"
 #include "pf12_device.cuh"
 #include "pf12_internal.h"
-#include "pf12_tc.cuh"
 
 namespace pf12 {
 
-// One pair, steps 1-5 (order of evaluation: At = Q^T A first, so that every
-// FP64 solve has k right-hand sides).
-//   M = [J_g ; At^g_i ; At^g_j]   ((m + 2k) x ld)  ->  [L ; Ct_i ; Ct_j]
-//   F = [At^f_i ; At^f_j]         (2k x ld)        ->  [At^f_i - Ct_i J_f ; At^f_j]
-//   V = (At^f_i - Ct_i J_f) Ct_j^T + Ct_i At^f_j^T
-__device__ __forceinline__ void write_pair_energy(const FwdParams& prm, int64_t P, const double e[3],
-                                                  double D, double X) {
-  prm.e_pair[3 * P + 0] = e[0];
-  prm.e_pair[3 * P + 1] = e[1];
-  prm.e_pair[3 * P + 2] = e[2];
-  prm.dx[2 * P] = D;
-  prm.dx[2 * P + 1] = X;
-  prm.status[P] = (isfinite(D) && isfinite(X)) ? 0 : 2;
-}
-
-template <typename TC>
-__device__ bool pair_forward(const FwdParams& prm, const PairDesc& pd, double* ws, GemmSmem& gs,
-                             CholSmem& cs, double (*red)[kThreads / 32], SieveCtl& sc,
-                             uint32_t& phase) {
-  const int tid = threadIdx.x;
-  const int p = pd.p, k = pd.k, m = pd.m;
-  const int64_t ld = (m + 3) / 4 * 4;
-  double* M = ws;
-  double* F = ws + (int64_t)(m + 2 * k) * ld;
-  const double* Jg = prm.Jg + pd.off_mm;
-  const double* Jf = prm.Jf + pd.off_mm;
-  const double* Q = prm.Q + pd.off_pk;
-  const double* T = prm.T + pd.off_kk;
-
-  // J_g -> M; a packed J_f is unpacked into the slab for its product
-  load_metric(Jg, m, prm.metric_packed, M, ld);
-  const double* Jf_use = Jf;
-  int64_t ld_jf = m;
-  if (prm.metric_packed) {
-    double* W = ws + fwd_jf_off(p, k, m, prm.gdesc != nullptr);
-    unpack_metric(Jf, m, W, ld);
-    Jf_use = W;
-    ld_jf = ld;
-  }
-
-  // S1: packed factors, or (gather mode) the pair's blocks sieved out of the
-  // per-orbital pair-extended blocks into the slab
-  const double* Asrc[4] = {prm.Agi + pd.off_pm, prm.Agj + pd.off_pm, prm.Afi + pd.off_pm,
-                           prm.Afj + pd.off_pm};
-  if (prm.gdesc) {
-    double* G = ws + fwd_sieve_off(k, m);
-    if (!sieve_pair(prm, pd, G, gs, sc, phase)) return false;
-    for (int x = 0; x < 4; ++x) Asrc[x] = G + (int64_t)x * p * m;
-  }
-  // S1': At^x = Q^T A^x  (k x m), A(a, mu) = Q[mu * k + a]
-  // SOMO-augmented pair: the first kq rows through Q, the SOMO rows copied
-  const int kq = k - pd.s;
-  double* Adst[4] = {M + (int64_t)m * ld, M + (int64_t)(m + k) * ld, F, F + (int64_t)k * ld};
-#pragma unroll 1
-  for (int x = 0; x < 4; ++x) {
-    cta_gemm<TC, true, false>(kq, m, p, Q, kq, Asrc[x], m, Adst[x], ld, 1.0, false, gs);
-    if (pd.s) copy_somo_rows(Asrc[x], p, pd.s, m, Adst[x], ld, kq);
-  }
-  if (pd.s) __syncthreads();
-
-  // S2: FP64 Cholesky of J_g with the forward solve of [At^g_i; At^g_j]
-  const bool ok = chol_augmented(M, ld, m, m + 2 * k, cs, gs);
-  if (!ok) {
-    if (tid == 0) {
-      const double nan = __longlong_as_double(0x7ff8000000000000ll);
-      prm.status[pd.pair] = 1;
-      prm.e_pair[3 * (int64_t)pd.pair + 0] = nan;
-      prm.e_pair[3 * (int64_t)pd.pair + 1] = nan;
-      prm.e_pair[3 * (int64_t)pd.pair + 2] = nan;
-      prm.dx[2 * (int64_t)pd.pair] = nan;
-      prm.dx[2 * (int64_t)pd.pair + 1] = nan;
-    }
-    return true;
-  }
-  double* Ci = M + (int64_t)m * ld;
-  double* Cj = M + (int64_t)(m + k) * ld;
-  // S2: FP64 backward solve  Ct = Y L^{-1}
-  solve_right_lower(M, ld, m, Ci, ld, 2 * k, cs, gs);
-
-  // S3: F_i <- At^f_i - Ct_i J_f ;  V = F_i Ct_j^T + Ct_i At^f_j^T
-  double* Fi = F;
-  double* Fj = F + (int64_t)k * ld;
-  cta_gemm<TC, false, false>(k, m, m, Ci, ld, Jf_use, ld_jf, Fi, ld, -1.0, true, gs);
-  double* V = prm.V + pd.off_kk;
-  for (int r0 = 0; r0 < k; r0 += kTile)
-    for (int c0 = 0; c0 < k; c0 += kTile) {
-      cta_gemm_tile<TC, false, true>(k, k, m, Fi, ld, Cj, ld, V, k, r0, c0, 1.0, false, gs);
-      cta_gemm_tile<TC, false, true>(k, k, m, Ci, ld, Fj, ld, V, k, r0, c0, 1.0, true, gs);
-    }
-  __syncthreads();
-  if (pd.s) {   // augmented pair: spin cases restricted to their own virtuals
-    double e[3], D, X;
-    somo_pair_energy(pd, V, T, red, e, D, X);
-    if (tid == 0) write_pair_energy(prm, pd.pair, e, D, X);
-    return true;
-  }
-
-  // S4: d = <V, T>, x = <V, T^T>   (FP64, fixed order)
-  double sd = 0.0, sx = 0.0;
-  for (int e = tid; e < k * k; e += kThreads) {
-    const int a = e / k, b = e - a * k;
-    const double v = V[e];
-    sd = fma(v, T[e], sd);
-    sx = fma(v, T[b * k + a], sx);
-  }
-  cta_sum2(sd, sx, red);
-  // S5: spin cases
-  if (tid == 0) {
-    const double e_ab = pd.n_ab * (3.0 * sd + sx) / 8.0;
-    const double e_aa = pd.n_aa * (sd - sx) / 4.0;
-    const double e_bb = pd.n_bb * (sd - sx) / 4.0;
-    const int64_t P = pd.pair;
-    prm.e_pair[3 * P + 0] = e_ab;
-    prm.e_pair[3 * P + 1] = e_aa;
-    prm.e_pair[3 * P + 2] = e_bb;
-    prm.dx[2 * P] = sd;
-    prm.dx[2 * P + 1] = sx;
-    prm.status[P] = (isfinite(sd) && isfinite(sx)) ? 0 : 2;
-  }
-  return true;
-}
-
-template <typename TC, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) pair_forward_kernel(FwdParams prm) {
-  __shared__ GemmSmem gs;
-  __shared__ CholSmem cs;
-  __shared__ double red[2][kThreads / 32];
-  __shared__ long long s_slot;
-  __shared__ SieveCtl sc;
-  uint32_t phase = 0;
-  if (prm.gdesc) sieve_init(sc);
-  double* ws = prm.work + (int64_t)blockIdx.x * prm.ws_stride;
-  int known_group = -1;
-  for (;;) {
-    if (threadIdx.x == 0) s_slot = next_slot(prm, known_group);
-    __syncthreads();
-    const long long slot = s_slot;
-    __syncthreads();
-    if (slot < 0 || slot >= prm.n_pairs) break;
-    const PairDesc pd = prm.desc[slot];
-    if (!pair_forward<TC>(prm, pd, ws, gs, cs, red, sc, phase)) {
-      if (threadIdx.x == 0) {
-        prm.status[pd.pair] = 3;
-        atomicExch(prm.err, 1);
-      }
-      break;
-    }
-    __syncthreads();
-  }
-}
-
-// Mixed-precision pair with the dense contractions on the tensor cores:
-// projections At^x = Q^T A^x and W = Ct_i J_f as tcgen05 split-TF32 GEMMs
-// (transposed tiles: m on the 128-row MMA axis, k on N), everything FP64
-// (Cholesky, solves, energy) unchanged.  Returns false after a bounded wait
-// expired (the pair gets status 3 and the kernel stops taking pairs).
-__device__ bool pair_forward_tc(const FwdParams& prm, const PairDesc& pd, double* ws, GemmSmem& gs,
-                                CholSmem& cs, double (*red)[kThreads / 32], tc::Stage& st,
-                                tc::Ctrl& ctrl, int* s_flag, SieveCtl& sc, uint32_t& phase) {
-  const int tid = threadIdx.x;
-  const int p = pd.p, k = pd.k, m = pd.m;
-  const int64_t ld = (m + 3) / 4 * 4;
-  double* M = ws;
-  double* F = ws + (int64_t)(m + 2 * k) * ld;
-  const double* Jg = prm.Jg + pd.off_mm;
-  const double* Jf = prm.Jf + pd.off_mm;
-  const double* Q = prm.Q + pd.off_pk;
-  const double* T = prm.T + pd.off_kk;
-  load_metric(Jg, m, prm.metric_packed, M, ld);
-  const double* Jf_use = Jf;
-  int64_t ld_jf = m;
-  if (prm.metric_packed) {
-    double* W = ws + fwd_jf_off(p, k, m, prm.gdesc != nullptr);
-    unpack_metric(Jf, m, W, ld);
-    Jf_use = W;
-    ld_jf = ld;
-  }
-  const double* Asrc[4] = {prm.Agi + pd.off_pm, prm.Agj + pd.off_pm, prm.Afi + pd.off_pm,
-                           prm.Afj + pd.off_pm};
-  if (prm.gdesc) {
-    double* G = ws + fwd_sieve_off(k, m);
-    if (!sieve_pair(prm, pd, G, gs, sc, phase)) return false;
-    for (int x = 0; x < 4; ++x) Asrc[x] = G + (int64_t)x * p * m;
-  }
-  const int kq = k - pd.s;
-  double* Adst[4] = {M + (int64_t)m * ld, M + (int64_t)(m + k) * ld, F, F + (int64_t)k * ld};
-#pragma unroll 1
-  for (int x = 0; x < 4; ++x) {
-    if (!tc::gemm<true, true>(m, kq, p, Asrc[x], m, Q, kq, Adst[x], ld, 1.0, false, st, ctrl, s_flag,
-                              prm.debug_wait_polls))
-      return false;
-    if (pd.s) copy_somo_rows(Asrc[x], p, pd.s, m, Adst[x], ld, kq);
-  }
-  __syncthreads();
-  const bool ok = chol_augmented(M, ld, m, m + 2 * k, cs, gs);
-  if (!ok) {
-    if (tid == 0) {
-      const double nan = __longlong_as_double(0x7ff8000000000000ll);
-      prm.status[pd.pair] = 1;
-      for (int q = 0; q < 3; ++q) prm.e_pair[3 * (int64_t)pd.pair + q] = nan;
-      prm.dx[2 * (int64_t)pd.pair] = nan;
-      prm.dx[2 * (int64_t)pd.pair + 1] = nan;
-    }
-    __syncthreads();
-    return true;
-  }
-  double* Ci = M + (int64_t)m * ld;
-  double* Cj = M + (int64_t)(m + k) * ld;
-  solve_right_lower(M, ld, m, Ci, ld, 2 * k, cs, gs);
-  double* Fi = F;
-  double* Fj = F + (int64_t)k * ld;
-  // F_i <- At^f_i - Ct_i J_f, computed as (J_f Ct_i^T)^T with J_f symmetric
-  if (!tc::gemm<false, false>(m, k, m, Jf_use, ld_jf, Ci, ld, Fi, ld, -1.0, true, st, ctrl, s_flag))
-    return false;
-  double* V = prm.V + pd.off_kk;
-  for (int r0 = 0; r0 < k; r0 += kTile)
-    for (int c0 = 0; c0 < k; c0 += kTile) {
-      cta_gemm_tile<float, false, true>(k, k, m, Fi, ld, Cj, ld, V, k, r0, c0, 1.0, false, gs);
-      cta_gemm_tile<float, false, true>(k, k, m, Ci, ld, Fj, ld, V, k, r0, c0, 1.0, true, gs);
-    }
-  __syncthreads();
-  if (pd.s) {
-    double e[3], D, X;
-    somo_pair_energy(pd, V, T, red, e, D, X);
-    if (tid == 0) write_pair_energy(prm, pd.pair, e, D, X);
-    return true;
-  }
-  double sd = 0.0, sx = 0.0;
-  for (int e = tid; e < k * k; e += kThreads) {
-    const int a = e / k, b = e - a * k;
-    const double v = V[e];
-    sd = fma(v, T[e], sd);
-    sx = fma(v, T[b * k + a], sx);
-  }
-  cta_sum2(sd, sx, red);
-  if (tid == 0) {
-    const int64_t P = pd.pair;
-    prm.e_pair[3 * P + 0] = pd.n_ab * (3.0 * sd + sx) / 8.0;
-    prm.e_pair[3 * P + 1] = pd.n_aa * (sd - sx) / 4.0;
-    prm.e_pair[3 * P + 2] = pd.n_bb * (sd - sx) / 4.0;
-    prm.dx[2 * P] = sd;
-    prm.dx[2 * P + 1] = sx;
-    prm.status[P] = (isfinite(sd) && isfinite(sx)) ? 0 : 2;
-  }
-  return true;
-}
-
-// shared memory of the tensor-core variant: the staging tiles share space with
-// the SIMT GEMM and Cholesky buffers (never live at the same time)
-constexpr size_t kTcUnion = sizeof(tc::Stage) > sizeof(GemmSmem) + sizeof(CholSmem)
-                                ? sizeof(tc::Stage)
-                                : sizeof(GemmSmem) + sizeof(CholSmem);
-constexpr size_t kTcSmem = kTcUnion + sizeof(tc::Ctrl) + 2 * (kThreads / 32) * sizeof(double) + 64;
-
-template <int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) pair_forward_tc_kernel(FwdParams prm) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  tc::Stage& st = *reinterpret_cast<tc::Stage*>(smem);
-  GemmSmem& gs = *reinterpret_cast<GemmSmem*>(smem);
-  CholSmem& cs = *reinterpret_cast<CholSmem*>(smem + sizeof(GemmSmem));
-  unsigned char* tail = smem + kTcUnion;
-  tc::Ctrl& ctrl = *reinterpret_cast<tc::Ctrl*>(tail);
-  double (*red)[kThreads / 32] = reinterpret_cast<double (*)[kThreads / 32]>(tail + sizeof(tc::Ctrl));
-  long long* s_slot = reinterpret_cast<long long*>(tail + sizeof(tc::Ctrl) + 2 * (kThreads / 32) * sizeof(double));
-  int* s_flag = reinterpret_cast<int*>(s_slot + 1);
-  __shared__ SieveCtl sc;
-  uint32_t phase = 0;
-  if (prm.gdesc) sieve_init(sc);
-  if (threadIdx.x == 0) *s_flag = 0;
-  tc::setup(ctrl);
-  double* ws = prm.work + (int64_t)blockIdx.x * prm.ws_stride;
-  int known_group = -1;
-  for (;;) {
-    if (threadIdx.x == 0) *s_slot = next_slot(prm, known_group);
-    __syncthreads();
-    const long long slot = *s_slot;
-    __syncthreads();
-    if (slot < 0 || slot >= prm.n_pairs) break;
-    const PairDesc pd = prm.desc[slot];
-    if (!pair_forward_tc(prm, pd, ws, gs, cs, red, st, ctrl, s_flag, sc, phase)) {
-      if (threadIdx.x == 0) {
-        prm.status[pd.pair] = 3;
-        atomicExch(prm.err, 1);
-      }
-      break;
-    }
-    __syncthreads();
-  }
-  tc::teardown(ctrl);
-}
-
-// Tile/occupancy variants the autotuner chooses from: variant 0 / 1 run the
-// SIMT kernel at MINB = 2 / 3 CTAs per SM (more resident pairs per SM hide the
+// Forward variants the autotuner chooses from: variant 0 / 1 run the SIMT
+// kernel at MINB = 2 / 3 CTAs per SM (more resident pairs per SM hide the
 // serial phases of each pair's factorisation; fewer leave more registers per
 // thread); variant 2 (mixed precision only) is the tensor-core kernel at 3.
-static cudaError_t tc_attr() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(pair_forward_tc_kernel<3>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-  // prefer the largest shared-memory carveout so that three 66 KB CTAs fit per SM
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(pair_forward_tc_kernel<3>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-  if (e == cudaSuccess) done = true;
-  return e;
-}
-
+// Each variant lives in its own translation unit under csrc/inst/.
 cudaError_t launch_forward(const FwdParams& prm, int precision, int variant, int n_ctas,
                            cudaStream_t s) {
   if (precision == 0) {
-    if (variant == 1) pair_forward_kernel<double, 3><<<n_ctas, kThreads, 0, s>>>(prm);
-    else pair_forward_kernel<double, 2><<<n_ctas, kThreads, 0, s>>>(prm);
-  } else if (variant == 2) {
-    cudaError_t e = tc_attr();
-    if (e != cudaSuccess) return e;
-    pair_forward_tc_kernel<3><<<n_ctas, kThreads, kTcSmem, s>>>(prm);
-  } else {
-    if (variant == 1) pair_forward_kernel<float, 3><<<n_ctas, kThreads, 0, s>>>(prm);
-    else pair_forward_kernel<float, 2><<<n_ctas, kThreads, 0, s>>>(prm);
+    if (variant == 1) return launch_fwd_f64_3(prm, n_ctas, s);
+    return launch_fwd_f64_2(prm, n_ctas, s);
   }
-  return cudaGetLastError();
+  if (variant == 2) return launch_fwd_tc_3(prm, n_ctas, s);
+  if (variant == 1) return launch_fwd_f32_3(prm, n_ctas, s);
+  return launch_fwd_f32_2(prm, n_ctas, s);
 }
 
 int forward_blocks_per_sm(int precision, int variant) {
-  int n = 0;
   if (precision == 0) {
-    if (variant == 1)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_kernel<double, 3>, kThreads, 0);
-    else if (variant == 0)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_kernel<double, 2>, kThreads, 0);
-  } else if (variant == 2) {
-    if (tc_attr() != cudaSuccess) return 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_tc_kernel<3>, kThreads, kTcSmem);
-    // resource model (registers, shared memory with the per-CTA reserve,
-    // threads); the runtime's answer for this dynamic-smem kernel can be lower
-    cudaFuncAttributes fa{};
-    int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0, reserve = 0;
-    if (cudaFuncGetAttributes(&fa, pair_forward_tc_kernel<3>) == cudaSuccess &&
-        cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess) {
-      const int by_regs = regs_sm / std::max(1, fa.numRegs * kThreads);
-      const int by_smem = smem_sm / (int)(fa.sharedSizeBytes + kTcSmem + reserve);
-      const int by_thr = thr_sm / kThreads;
-      n = std::max(n, std::min(by_regs, std::min(by_smem, by_thr)));
-    }
-    n = std::min(n, 4);  // 4 x 128 TMEM columns per SM at most
-  } else {
-    if (variant == 1)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_kernel<float, 3>, kThreads, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_forward_kernel<float, 2>, kThreads, 0);
+    if (variant == 1) return occupancy_fwd_f64_3();
+    if (variant == 0) return occupancy_fwd_f64_2();
+    return 0;
   }
-  return n;
+  if (variant == 2) return occupancy_fwd_tc_3();
+  if (variant == 1) return occupancy_fwd_f32_3();
+  return occupancy_fwd_f32_2();
 }
 
 // Deterministic total: thread t sums a contiguous range of pairs in order,
@@ -472,6 +137,17 @@ extern "C" int pf12_energy_noalloc(int32_t n_orb, const int8_t* kind, int64_t n_
                                    const pf12_tensors* t, int32_t precision, void* stream,
                                    double* V_dev, double* e_pair_dev, double* E_host) {
   using namespace pf12;
+  // every call copies from host stack memory, synchronises the stream and
+  // reads the result back: a capturing stream cannot take that, so refuse it
+  // before any other CUDA call touches (and would invalidate) the capture
+  {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap) != cudaSuccess) {
+      cudaGetLastError();
+      return PF12_ERR_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return PF12_ERR_UNSUPPORTED;
+  }
   if (precision != PF12_FP64 && precision != PF12_MIXED_FP32) return PF12_ERR_UNSUPPORTED;
   if (n_pairs < 0 || n_orb < 0) return PF12_ERR_INVALID_ARG;
   if (n_pairs == 0) {

@@ -109,6 +109,28 @@ inline int64_t bwd_ws(int p, int k, int m, bool gather = false, bool packed = fa
          (gather ? 4 * (int64_t)p * m + 64 : 0);
 }
 
+// Per-variant launchers and occupancy queries (one translation unit each,
+// csrc/inst/, compiled in parallel): f64 / f32 = product type, 2 / 3 = CTAs
+// per SM, tc = tcgen05 split-TF32 contractions.
+cudaError_t launch_fwd_f64_2(const FwdParams& prm, int n_ctas, cudaStream_t s);
+cudaError_t launch_fwd_f64_3(const FwdParams& prm, int n_ctas, cudaStream_t s);
+cudaError_t launch_fwd_f32_2(const FwdParams& prm, int n_ctas, cudaStream_t s);
+cudaError_t launch_fwd_f32_3(const FwdParams& prm, int n_ctas, cudaStream_t s);
+cudaError_t launch_fwd_tc_3(const FwdParams& prm, int n_ctas, cudaStream_t s);
+int occupancy_fwd_f64_2();
+int occupancy_fwd_f64_3();
+int occupancy_fwd_f32_2();
+int occupancy_fwd_f32_3();
+int occupancy_fwd_tc_3();
+cudaError_t launch_bwd_f64_2(const BwdParams& prm, int n_ctas, cudaStream_t s);
+cudaError_t launch_bwd_f64_3(const BwdParams& prm, int n_ctas, cudaStream_t s);
+cudaError_t launch_bwd_f32_2(const BwdParams& prm, int n_ctas, cudaStream_t s);
+cudaError_t launch_bwd_f32_3(const BwdParams& prm, int n_ctas, cudaStream_t s);
+int occupancy_bwd_f64_2();
+int occupancy_bwd_f64_3();
+int occupancy_bwd_f32_2();
+int occupancy_bwd_f32_3();
+
 constexpr int kFwdVariants = 3;
 cudaError_t launch_forward(const FwdParams& prm, int precision, int variant, int n_ctas,
                            cudaStream_t s);

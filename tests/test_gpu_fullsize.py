@@ -115,7 +115,7 @@ def test_c40h81_backward_full_list(built):
     for n, P in enumerate(pairs):
         got = grad_blocks(wl, lay, grads["fp64"], P)
         for name, want in ref["grads"][n].items():
-            assert np.abs(got[name] - want).max() <= 1e-9 * np.abs(want).max(), (P, name)
+            assert np.abs(got[name] - want).max() <= 1e-10 * np.abs(want).max(), (P, name)
     for name in names:
         a, b = grads["mixed_fp32"][name], grads["fp64"][name]
         assert np.abs(a - b).max() <= 2e-5 * np.abs(b).max(), name

@@ -1,9 +1,14 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
 Bars: FP64 mode within 1e-10 Eh per pair; mixed mode within 1 uEh in total
-after the chemical-scale normalisation (reading G1), gradients within 1e-9
-(FP64) of the oracle's, relative to the largest entry of each block.
+after the chemical-scale normalisation (reading G1); FP64 gradients within
+1e-10 of the oracle's, relative to the largest entry of each block; mixed-mode
+gradients within 2e-5 (the error model of the FP32 products: about
+sqrt(128) 2^-24 per promoted 128-wide span, amplified by cond(J_g) ~ 40 in the
+solves, so 0.75 cond(J_g) sqrt(128) 2^-24).
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -119,6 +124,55 @@ def test_not_spd_pair_is_reported(built):
     assert np.abs(np.delete(e, bad, axis=0) - ref["e_pair"]).max() <= 1e-10
 
 
+def test_workspace_cap_too_small_is_oom(built):
+    """Failure detection on the host: a workspace cap below one slab of the
+    largest pair is refused with PF12_ERR_OOM at upload, and the same context
+    then works for a list that fits under a sufficient cap."""
+    import paper_2008_03237_gb300 as pf
+    wl = S.tiny()
+    t, lay = upload_host(wl)
+    eng = pf.PairF12("fp64", workspace_bytes=4096)
+    with pytest.raises(pf.Pf12Error) as ei:
+        eng.upload_pairs(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
+    assert ei.value.code == -3
+    eng.close()
+    eng = pf.PairF12("fp64", workspace_bytes=64 << 20)
+    eng.upload_pairs(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
+    eng.fit()
+    E, _ = eng.energy()
+    assert abs(E - O.run(wl)["E"]) <= 1e-10
+
+
+def test_backward_not_spd_pair_gets_zero_gradients(built):
+    """An indefinite J_g in one pair: the adjoint marks it NOT_SPD and writes
+    zeros into that pair's gradient blocks (a stale value from an earlier call
+    must not survive); the other pairs keep their oracle gradients."""
+    import paper_2008_03237_gb300 as pf
+    wl = S.tiny()
+    host, lay = S.packed_inputs(wl)
+    bad = 5
+    m = int(wl.n_aux[bad])
+    o = lay["off_mm"][bad]
+    host["Jg"][o:o + m * m].reshape(m, m)[...] -= 20.0 * np.eye(m)
+    t, lay = upload_host(wl, (host, lay))
+    eng = pf.PairF12("fp64")
+    eng.upload_pairs(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
+    g = {n: torch.full_like(t[n], 7.0) for n in ("Agi", "Agj", "Afi", "Afj", "Q", "T")}
+    eng.backward(1.0, g)
+    torch.cuda.synchronize()
+    assert eng.pair_status()[bad] == 1
+    gh = {n: v.cpu().numpy() for n, v in g.items()}
+    blocks = grad_blocks(wl, lay, gh, bad)
+    for n, v in blocks.items():
+        assert (v == 0.0).all(), n
+    keep = [P for P in range(wl.n_pairs) if P != bad]
+    ref = O.run(wl, pairs=keep, want_grad=True)
+    for q, P in enumerate(keep):
+        got = grad_blocks(wl, lay, gh, P)
+        for n, want in ref["grads"][q].items():
+            assert np.abs(got[n] - want).max() <= 1e-10 * max(np.abs(want).max(), 1e-300), (P, n)
+
+
 def test_unavailable_variant_is_refused(built):
     import paper_2008_03237_gb300 as pf
     wl = S.tiny()
@@ -163,7 +217,7 @@ def test_backward_fp64(built, make):
         got = grad_blocks(wl, r["lay"], r["grads"], P)
         for n, want in ref["grads"][P].items():
             scale = max(np.abs(want).max(), 1e-300)
-            assert np.abs(got[n] - want).max() <= 1e-9 * scale, (P, n)
+            assert np.abs(got[n] - want).max() <= 1e-10 * scale, (P, n)
 
 
 def test_backward_mixed(built):
@@ -177,41 +231,80 @@ def test_backward_mixed(built):
             assert np.abs(got[n] - want).max() <= 2e-5 * scale, (P, n)
 
 
-def test_autograd_function_and_finite_differences(built):
+def test_autograd_saves_inputs_and_second_backward(built):
+    """The autograd function keeps its inputs alive (save_for_backward) and a
+    second backward (retain_graph=True) gives the same gradients from a new
+    engine; an in-place change of an input before backward is refused."""
     import paper_2008_03237_gb300 as pf
     wl = S.custom(3, 1, None, (20, 40), ("uniform", 3, 12), (20, 70), name="autograd")
     t, lay = upload_host(wl)
     meta = dict(lay, n_orb=wl.n_orb, orb_kind=wl.orb_kind, pi=wl.pi, pj=wl.pj, n_pao=wl.n_pao,
                 n_pno=wl.n_pno, n_aux=wl.n_aux, precision="fp64")
-    leaves = {n: t[n].clone().requires_grad_(n not in ("Jg", "Jf"))
-              for n in ("Agi", "Agj", "Afi", "Afj", "Jg", "Jf", "Q", "T")}
-    E = pf.pair_f12_energy(*[leaves[n] for n in ("Agi", "Agj", "Afi", "Afj", "Jg", "Jf", "Q", "T")],
-                           meta)
+    names = ("Agi", "Agj", "Afi", "Afj", "Jg", "Jf", "Q", "T")
+    leaves = {n: t[n].clone().requires_grad_(n not in ("Jg", "Jf")) for n in names}
+    # a temporary input: its storage must survive until backward
+    E = pf.pair_f12_energy(*[leaves[n] * 1.0 if n == "Afi" else leaves[n] for n in names], meta)
+    E.backward(retain_graph=True)
+    g1 = {n: leaves[n].grad.clone() for n in ("Agi", "Afi", "Q", "T")}
+    for n in g1:
+        leaves[n].grad = None
     E.backward()
+    for n in g1:
+        assert torch.equal(leaves[n].grad, g1[n]), n
     ref = O.run(wl)
     assert abs(E.item() - ref["E"]) <= 1e-10
-    rng = np.random.default_rng(7)
+    x = t["T"].clone().requires_grad_(True)
+    y = x * 1.0
+    E2 = pf.pair_f12_energy(*[y if n == "T" else t[n] for n in names], meta)
+    y.add_(1.0)
+    with pytest.raises(RuntimeError):
+        E2.backward()
+
+
+def test_autograd_finite_differences_c40h81(built):
+    """Central finite differences of E through the autograd function on the
+    C40H81 chain (2,821 pairs, FP64): 20 random unit directions per tensor
+    group (not tilted towards the gradient), h = 1e-5.  E is linear in each
+    of A^g_i, A^g_j, A^f_i, A^f_j and T and quadratic in Q, so the central
+    difference has no truncation error and only rounding separates it from the
+    directional derivative; the bound is 1e-7 relative plus that rounding
+    noise, 20 u sum_P |e_P| / h (u = 2^-53), and the directions' median
+    signal-to-noise ratio must exceed 100 so that the check is not vacuous."""
+    import paper_2008_03237_gb300 as pf
+    from synthetic import device
+    wl = S.c40h81()
+    t, lay = device.allocate(wl)
+    device.fill(wl, t, lay)
+    meta = dict(lay, n_orb=wl.n_orb, orb_kind=wl.orb_kind, pi=wl.pi, pj=wl.pj, n_pao=wl.n_pao,
+                n_pno=wl.n_pno, n_aux=wl.n_aux, precision="fp64", variant=1)
+    names = ("Agi", "Agj", "Afi", "Afj", "Jg", "Jf", "Q", "T")
+    leaves = {n: t[n].requires_grad_(n not in ("Jg", "Jf")) for n in names}
+    E = pf.pair_f12_energy(*[leaves[n] for n in names], meta)
+    E.backward()
+    grads = {n: leaves[n].grad.detach() for n in ("Agi", "Agj", "Afi", "Afj", "Q", "T")}
+    for n in names:
+        leaves[n].requires_grad_(False)
+        leaves[n].grad = None
+    ref = np.load(os.path.join(os.path.dirname(__file__), "golden", "c40h81_oracle.npz"))
+    assert abs(E.item() - float(ref["E"])) <= 1e-9
     h = 1e-5
-    E0 = abs(E.item())
-    for n in ("Agi", "Agj", "Afi", "Afj", "Q", "T"):
-        g = leaves[n].grad
-        gn = g / g.norm()
-        for _ in range(5):
-            # random unit directions tilted towards the gradient, so that the
-            # directional derivative stands well above the FD rounding noise
-            r = torch.from_numpy(rng.standard_normal(t[n].numel())).cuda()
-            d = gn + r / r.norm()
-            d /= d.norm()
-            ep = pf.pair_f12_energy(*[(t[x] + h * d) if x == n else t[x]
-                                      for x in ("Agi", "Agj", "Afi", "Afj", "Jg", "Jf", "Q", "T")],
-                                    meta).item()
-            em = pf.pair_f12_energy(*[(t[x] - h * d) if x == n else t[x]
-                                      for x in ("Agi", "Agj", "Afi", "Afj", "Jg", "Jf", "Q", "T")],
-                                    meta).item()
-            fd = (ep - em) / (2 * h)
-            an = float((g * d).sum())
-            noise = 8 * 2.2e-16 * E0 / h
-            assert abs(fd - an) <= 1e-7 * abs(an) + noise, (n, fd, an)
+    noise = 20 * 2.0 ** -53 * float(ref["sum_abs"]) / h
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(20080323)
+    with torch.no_grad():
+        for n, g in grads.items():
+            snr = []
+            for _ in range(20):
+                d = torch.randn(t[n].numel(), generator=gen, device="cuda", dtype=torch.float64)
+                d /= d.norm()
+                ep = pf.pair_f12_energy(*[(t[x] + h * d) if x == n else t[x] for x in names], meta).item()
+                em = pf.pair_f12_energy(*[(t[x] - h * d) if x == n else t[x] for x in names], meta).item()
+                fd = (ep - em) / (2 * h)
+                an = float((g * d).sum())
+                assert abs(fd - an) <= 1e-7 * abs(an) + noise, (n, fd, an, noise)
+                snr.append(abs(an) / noise)
+                del d
+            assert np.median(snr) > 100, (n, np.median(snr))
 
 
 def test_bounded_wait_expiry_is_reported_and_context_survives(built):
