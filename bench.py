@@ -78,6 +78,9 @@ def parse():
                     help="SOMO-augmented PNO space (no e2e or CPU legs)")
     ap.add_argument("--variant", type=int, default=None,
                     help="force a forward kernel variant instead of autotuning (profiling)")
+    ap.add_argument("--full", action="store_true",
+                    help="the complete pair energy E_(2)F12 (every term of Eqs. Vtilde, Btilde "
+                         "with the PNO projector) instead of the amplitude term alone")
     return ap.parse_args()
 
 
@@ -598,6 +601,8 @@ def main():
         return run_streamed(args, rank, world, local_rank)
     if args.shard and world > 1:
         return run_sharded(args, rank, world, local_rank)
+    if args.full:
+        return run_full(args, rank, world, local_rank)
     wl, f64, fmix, byts, o = run_ours(args, rank, world, local_rank)
     ms = o["ms"]
     if world > 1:
@@ -671,6 +676,97 @@ def main():
         line["cpu_baseline_1thread"] = {"value": rate1, "unit": "pairs/s", "cores": 1,
                                         "kind": "oracle", "sample": sample1}
     print(json.dumps(line), flush=True)
+
+
+def full_flops(wl):
+    """Algorithmic FP64 flops (factorisation + solves on 4p + 4 right-hand
+    sides), mixable flops and input bytes of one full-energy pass."""
+    p, k, m = (wl.n_pao.astype(float), wl.n_pno.astype(float), wl.n_aux.astype(float))
+    k2 = k + 2
+    f64 = float((m ** 3 / 3 + 2 * (4 * p + 4) * m * m).sum())
+    fmix = float((8 * p * k * m + 2 * k2 * m * m + 4 * k2 * k2 * m + 4 * p * m * m
+                  + 12 * p * p * m + 8 * p * p * k + 12 * p * k * k + 2 * k * k * k2 * m
+                  + 2 * k * k2 * k2 * m + 4 * p ** 3).sum())
+    byts = float((8 * (10 * (p + 2) * m + 3 * m * m + p * k + k * k + p * p + 2 * k
+                       + k * m * k2)).sum())
+    return f64, fmix, byts
+
+
+def run_full(args, rank, world, local_rank):
+    """The complete pair energy on one workload (default C40H81, whose inputs
+    stay resident): mixed precision timed as the headline, the FP64 mode beside
+    it, and the error of the mixed energies against FP64 on the chemical scale."""
+    import torch
+
+    import __graft_entry__
+    import paper_2008_03237_gb300 as pf
+    from synthetic import device
+    torch.cuda.set_device(local_rank)
+    __graft_entry__.build()
+    name = args.workload if args.workload != "c160h321" or args.max_pairs else "c40h81"
+    wl = make_workload(name, args.max_pairs, rank)
+    f64, fmix, byts = full_flops(wl)
+    t, lay = device.allocate_full(wl)
+    device.fill_full(wl, t, lay)
+    res = {}
+    for prec in (args.precision, "fp64") if args.precision != "fp64" else ("fp64",):
+        eng = pf.PairF12(prec, variant=args.variant)
+        eng.upload_full(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
+        steps = args.steps if prec == args.precision else max(2, args.steps // 2)
+        for _ in range(args.warmup if prec == args.precision else 1):
+            eng.fit()
+            eng.energy(want_host=False)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local_rank) if prec == args.precision else _Null()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with sampler:
+            ev0.record()
+            for _ in range(steps):
+                eng.fit()
+                eng.energy(want_host=False)
+            ev1.record()
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        E, e = eng.energy()
+        st = eng.stats()
+        res[prec] = {"ms": ms, "ms_fit": st["ms_fit"], "E": E, "e": e.cpu().numpy(),
+                     "bad": int((eng.pair_status() != 0).sum()), "variant": st["tile_config"],
+                     "tune_ms": st["tune_ms"][:2],
+                     "clocks": sampler.summary() if prec == args.precision else None}
+        eng.close()
+    head = res[args.precision]
+    line = {"metric": METRIC, "value": wl.n_pairs / head["ms"] * 1e3, "unit": "pairs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32" if args.precision != "fp64" else "f64",
+            "data": "synthetic (seeded Philox4x32-10 draws, device-resident)",
+            "config": {"workload": wl.name, "pairs": wl.n_pairs, "precision": args.precision,
+                       "energy": "complete E_(2)F12 per pair (occupied, amplitude, C and singles "
+                                 "terms of Vtilde; B~ with i_F, j_F; PNO projector term)",
+                       "l2": f"inputs {byts / 1e9:.0f} GB >> 129 MB L2, no flush"},
+            "tflops": {"fp64": f64 / head["ms_fit"] / 1e9, "mixed_part": fmix / head["ms_fit"] / 1e9},
+            "roofline": {"bound": "alu", "achieved": (f64 + (fmix if args.precision == "fp64" else 0))
+                         / head["ms_fit"] / 1e9, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "kernel": "pair_full_kernel (fused persistent)",
+                         "ms_per_launch": head["ms_fit"], "traffic": None},
+            "clocks": head["clocks"], "gpu_launches": 2 * args.steps, "e2e": None,
+            "E_total_raw": head["E"], "pairs_failed": head["bad"],
+            "autotuner": {"variant": head["variant"], "sample_ms": head["tune_ms"],
+                          "variants": ["2 CTAs/SM", "3 CTAs/SM"]}}
+    line["roofline"]["frac"] = line["roofline"]["achieved"] / FP64_PEAK_TFLOPS
+    if "fp64" in res and args.precision != "fp64":
+        r64 = res["fp64"]
+        sum_abs = float(np.abs(r64["e"].sum(axis=1)).sum())
+        kappa = CHEM_SCALE_PER_ORB * wl.n_orb / sum_abs
+        line["fp64_mode"] = {"value": wl.n_pairs / r64["ms"] * 1e3, "ms_per_step": r64["ms"],
+                             "fp64_tflops": (f64 + fmix) / r64["ms_fit"] / 1e9,
+                             "frac_of_fp64_peak": (f64 + fmix) / r64["ms_fit"] / 1e9 / FP64_PEAK_TFLOPS}
+        line["error_vs_fp64"] = {"total_Eh_normalised": abs(head["E"] - r64["E"]) * kappa,
+                                 "max_pair_Eh_normalised": float(np.abs(head["e"] - r64["e"]).max() * kappa),
+                                 "kappa": kappa}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_sharded(args, rank, world, local_rank):

@@ -301,6 +301,95 @@ int pf12_upload_pairs_gather(pf12_ctx* ctx, int32_t n_orb, const int8_t* orb_kin
 int pf12_backward_gather(pf12_ctx* ctx, double dE, double* dBg, double* dBf, double* dQ,
                          double* dT);
 
+/* ------------------------------------------------------------------------
+ * Complete pair energy ("full mode"): every term of E_(2)F12 = sum_{i<j}
+ * 2 Vt^{ij}_{ij} + B~^{ij}_{ij} (Eq. F12 energy), per pair:
+ *   Vt (Eq. Vtilde)  occupied block V^{ij}_{ij}, amplitude term 1/2 V_ab t^ab,
+ *                    Fock-coupling term 1/2 C_ab t^ab (Eq. C) and the singles
+ *                    terms V^{ij}_{i a_j} t^{a_j}_j + V^{ij}_{a_i j} t^{a_i}_i
+ *   V  (Eq. V)       robust fit of the V kernel with the Q_ij projector
+ *                    (Eq. Qij): the part of the geminal on PNO pairs removed
+ *                    through the PNO-pair factors
+ *   B~ (Eqs. B, X, Btilde, XAppr)  B - X^{i j_F} - X^{i_F j} with the
+ *                    Fock-transformed occupied orbitals (pair decoupling)
+ * then the spin-adapted energies (Eqs. F12energy_sf*).  The pair's PAO
+ * domain (orthonormal) stands in for the complete virtual space of the sums in
+ * Eqs. C, B and X, so the fit runs in the PAO domain: FP64 solves on 4p + 4
+ * right-hand sides (the PAOs and i, j for both orbitals, and the PAOs for i_F
+ * and j_F).  In spatial terms, per pair,
+ *   Vt_d = 1/2 (Vh[i,j] + <Vh,T> + Vh[i,s_j] + Vh[s_i,j]) + <C,T>
+ *   Vt_x = 1/2 (Vh[j,i] + <Vh,T^T> + Vh[j,s_i] + Vh[s_j,i]) + <C,T^T>
+ *   B~_dd = tr(R F R^T) + tr(R^T F R) - <K_jF, R> - <K_iF, R>
+ *   B~_dx = 2 tr(R F R) - <K_jF, R^T> - <K_iF, R^T>
+ *   e_ab = n_ab (3/4 Vt_d + 1/4 Vt_x + (10 B~_dd + 6 B~_dx)/64)
+ *   e_aa = n_aa (1/2 (Vt_d - Vt_x) + (B~_dd - B~_dx)/16),  e_bb likewise
+ * with R the projected geminal over the PAO domain, F the virtual Fock block,
+ * Vh the projected V over the PNOs and i, j, and C = Ft^T K Q + Q^T K Ft,
+ * Ft = (1 - Q Q^T) F Q.
+ *
+ * Per-pair tensors, pair P's blocks at element offset off_xx[P] (multiples of
+ * 2) of the matching buffer, all float64 row-major:
+ *   Ag_i .. ArF_j : (p + 2) x m at off_pm.  Rows 0..p-1 are the PAOs; rows p
+ *        and p + 1 are the occupied orbitals i and j as bra functions, used
+ *        by Ag_*, Af_* only (row p + 1 of the i blocks equals row p of the j
+ *        blocks: (ij|X)).  Ag: Coulomb factors; Af: V-kernel factors; Ar:
+ *        geminal factors; AgF_*, ArF_*: the same for the Fock-transformed
+ *        occupied orbitals i_F, j_F
+ *   Jg, Jf, Jr    : m x m at off_mm (SPD metrics of the three operators)
+ *   Q : p x k at off_pk;  T : k x k at off_kk
+ *   Fv : p x p at off_pp (Fock matrix over the PAO domain, symmetric)
+ *   S  : 2 x k at off_s (singles amplitudes of i, then j, in the pair's PNOs)
+ *   B  : k x m x (k + 2) at off_b: B[c][X][q] = (c q|X) contracted with the
+ *        Coulomb metric's inverse square root, q over the PNOs, then i, then j
+ * Limits: 1 <= k <= p, m <= 4096, k <= 256.
+ * Gather mode, SOMO augmentation, packed metrics, streamed inputs, V output
+ * and the adjoint are not offered in full mode (PF12_ERR_UNSUPPORTED). */
+typedef struct {
+  const double* Ag_i;
+  const double* Ag_j;
+  const double* Af_i;
+  const double* Af_j;
+  const double* Ar_i;
+  const double* Ar_j;
+  const double* AgF_i;
+  const double* AgF_j;
+  const double* ArF_i;
+  const double* ArF_j;
+  const double* Jg;
+  const double* Jf;
+  const double* Jr;
+  const double* Q;
+  const double* T;
+  const double* Fv;
+  const double* S;
+  const double* B;
+  const int64_t* off_pm; /* host */
+  const int64_t* off_mm; /* host */
+  const int64_t* off_pk; /* host */
+  const int64_t* off_kk; /* host */
+  const int64_t* off_pp; /* host */
+  const int64_t* off_s;  /* host */
+  const int64_t* off_b;  /* host */
+  int64_t len_pm, len_mm, len_pk, len_kk, len_pp, len_s, len_b;
+} pf12_full_tensors;
+
+#define PF12_FULL_TERMS 14 /* per-pair spatial terms written by pf12_full_terms */
+
+/* Register a pair list for the complete pair energy (arguments as
+ * pf12_upload_pairs, tensors as above).  pf12_fit then evaluates every term
+ * for every pair in one persistent launch and pf12_energy returns the
+ * spin-case pair energies and the total as in the amplitude-only mode. */
+int pf12_upload_full(pf12_ctx* ctx, int32_t n_orb, const int8_t* orb_kind, int64_t n_pairs,
+                     const int32_t* pi, const int32_t* pj, const int32_t* n_pao,
+                     const int32_t* n_pno, const int32_t* n_aux, const pf12_full_tensors* t);
+
+/* Full mode: copy the per-pair spatial terms of the last pf12_fit into
+ * terms_dev (device, n_pairs x PF12_FULL_TERMS, caller's pair order):
+ *   0 Vh[i,j]  1 Vh[j,i]  2 <Vh,T>  3 <Vh,T^T>  4 singles (direct)
+ *   5 singles (exchange)  6 <C,T>  7 <C,T^T>  8 B_dd  9 B_dx
+ *   10 <K_jF,R>  11 <K_jF,R^T>  12 <K_iF,R>  13 <K_iF,R^T> */
+int pf12_full_terms(pf12_ctx* ctx, double* terms_dev);
+
 /* Allocation-free forward pass: steps 1-6 for every pair in one call, with
  * no cudaMalloc, cudaFree or other allocating call.  The paper has no
  * counterpart; this entry point exists for callers that cannot allocate

@@ -183,6 +183,42 @@ class PairF12:
         self.n_pairs = n
         self.len_kk = g.len_kk
 
+    # python names of the full-mode tensors, in the order of _lib.FULL_FACTORS / FULL_OTHERS
+    FULL_NAMES = ("Agi", "Agj", "Afi", "Afj", "Ari", "Arj", "AgiF", "AgjF", "AriF", "ArjF",
+                  "Jg", "Jf", "Jr", "Q", "T", "Fv", "S", "B")
+
+    def upload_full(self, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, tensors, offsets):
+        """Complete pair energy (pf12_upload_full).  tensors: dict of packed
+        float64 CUDA tensors named as FULL_NAMES; offsets: off_pm, off_mm,
+        off_pk, off_kk, off_pp, off_s, off_b (int64 host arrays)."""
+        self._stream()
+        kind = np.ascontiguousarray(np.asarray(orb_kind, dtype=np.int8))
+        meta = [_i32(pi), _i32(pj), _i32(n_pao), _i32(n_pno), _i32(n_aux)]
+        offs = {n: _i64(offsets[n]) for n in _lib.FULL_OFFSETS}
+        ft = _lib.FullTensors()
+        for py, c in zip(self.FULL_NAMES, _lib.FULL_FACTORS + _lib.FULL_OTHERS):
+            setattr(ft, c, _dev(tensors[py], py))
+        for n in _lib.FULL_OFFSETS:
+            setattr(ft, n, _ptr(offs[n], ctypes.c_int64))
+        lens = {"len_pm": "Agi", "len_mm": "Jg", "len_pk": "Q", "len_kk": "T", "len_pp": "Fv",
+                "len_s": "S", "len_b": "B"}
+        for n, src in lens.items():
+            setattr(ft, n, tensors[src].numel())
+        n = len(meta[0])
+        self._check(self._L.pf12_upload_full(
+            self._h, int(n_orb), _ptr(kind, ctypes.c_int8), n,
+            *[_ptr(a, ctypes.c_int32) for a in meta], ctypes.byref(ft)))
+        self._keep = (tensors, offs, meta, kind)
+        self.n_pairs = n
+
+    def full_terms(self, terms=None):
+        """Per-pair spatial terms of the last full-mode fit (n_pairs x 14)."""
+        self._stream()
+        if terms is None:
+            terms = torch.zeros((self.n_pairs, 14), dtype=torch.float64, device="cuda")
+        self._check(self._L.pf12_full_terms(self._h, _dev(terms, "terms")))
+        return terms
+
     def backward_gather(self, dE=1.0, grads=None):
         """Gather mode: dE * dE_F12/d{Bg, Bf} (per-orbital blocks), dQ, dT."""
         self._stream()

@@ -40,6 +40,17 @@ class GatherTensors(ctypes.Structure):
                 ("len_mm", ctypes.c_int64), ("len_pk", ctypes.c_int64), ("len_kk", ctypes.c_int64)]
 
 
+FULL_FACTORS = ("Ag_i", "Ag_j", "Af_i", "Af_j", "Ar_i", "Ar_j", "AgF_i", "AgF_j", "ArF_i", "ArF_j")
+FULL_OTHERS = ("Jg", "Jf", "Jr", "Q", "T", "Fv", "S", "B")
+FULL_OFFSETS = ("off_pm", "off_mm", "off_pk", "off_kk", "off_pp", "off_s", "off_b")
+
+
+class FullTensors(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in FULL_FACTORS + FULL_OTHERS] + \
+               [(n, c_i64p) for n in FULL_OFFSETS] + \
+               [("len_" + n[4:], ctypes.c_int64) for n in FULL_OFFSETS]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("ms_fit", ctypes.c_double), ("ms_energy", ctypes.c_double),
                 ("ms_backward", ctypes.c_double), ("flops_fp64", ctypes.c_double),
@@ -72,6 +83,10 @@ SIGNATURES = {
                                                 ctypes.c_int64, c_i32p, c_i32p, c_i32p, c_i32p,
                                                 c_i32p, ctypes.POINTER(GatherTensors)]),
     "pf12_backward_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double] + [ctypes.c_void_p] * 4),
+    "pf12_upload_full": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, c_i8p, ctypes.c_int64,
+                                        c_i32p, c_i32p, c_i32p, c_i32p, c_i32p,
+                                        ctypes.POINTER(FullTensors)]),
+    "pf12_full_terms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "pf12_energy_noalloc": (ctypes.c_int, [ctypes.c_int32, c_i8p, ctypes.c_int64, c_i32p, c_i32p,
                                            c_i32p, c_i32p, c_i32p, ctypes.POINTER(Tensors),
                                            ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,

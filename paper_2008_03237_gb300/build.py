@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libpairf12.so")
 # host-side translation units, then one per kernel variant (csrc/inst/): the
 # variants are large fused kernels, and compiling them apart lets them build
 # in parallel
-SOURCES = ["pf12_api.cu", "pf12_forward.cu", "pf12_backward.cu"] + sorted(
+SOURCES = ["pf12_api.cu", "pf12_forward.cu", "pf12_backward.cu", "pf12_full.cu"] + sorted(
     os.path.join("inst", f) for f in os.listdir(os.path.join(CSRC, "inst")) if f.endswith(".cu"))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

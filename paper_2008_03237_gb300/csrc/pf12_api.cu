@@ -100,6 +100,15 @@ struct pf12_ctx {
   int32_t* d_slot_group = nullptr;
   size_t cap_sg = 0;
 
+  // full mode: the complete pair energy (pf12_upload_full)
+  bool full = false;
+  pf12_full_tensors ft{};
+  pf12::FullDesc* d_fdesc = nullptr;
+  pf12::FullDesc* d_fdesc_sample = nullptr;
+  double* d_terms = nullptr;
+  size_t cap_fdesc = 0, cap_fsample = 0, cap_terms = 0;
+  int n_ctas_full_v[pf12::kFullVariants] = {};
+
   // graph of the forward launch
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -160,6 +169,7 @@ void free_pairs(pf12_ctx* c) {
   c->arr_ready = nullptr;
   c->arr_dirty = false;
   c->gather = false;
+  c->full = false;
   c->uploaded = c->fitted = false;
   c->n_pairs = 0;
 }
@@ -169,7 +179,8 @@ void release_all(pf12_ctx* c) {
   void* ptrs[] = {c->d_desc, c->d_gdesc, c->d_desc_by_pair, c->d_map_pao, c->d_map_aux,
                   c->d_orb_ptr, c->d_orb_list, c->d_off_orb, c->d_ld_orb, c->d_dA,
                   c->d_desc_sample, c->d_V, c->d_epair, c->d_dx, c->d_status, c->d_out3,
-                  c->d_counter, c->d_work, c->d_tmaps, c->d_slot_group};
+                  c->d_counter, c->d_work, c->d_tmaps, c->d_slot_group, c->d_fdesc,
+                  c->d_fdesc_sample, c->d_terms};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -763,12 +774,279 @@ int tune(pf12_ctx* c) {
 
 }  // namespace
 
+namespace {
+
+// ------------------------------------------------------------------ full mode
+
+pf12::FullParams full_params(pf12_ctx* c) {
+  pf12::FullParams f{};
+  const pf12_full_tensors& t = c->ft;
+  f.Agi = t.Ag_i;
+  f.Agj = t.Ag_j;
+  f.Afi = t.Af_i;
+  f.Afj = t.Af_j;
+  f.Ari = t.Ar_i;
+  f.Arj = t.Ar_j;
+  f.AgiF = t.AgF_i;
+  f.AgjF = t.AgF_j;
+  f.AriF = t.ArF_i;
+  f.ArjF = t.ArF_j;
+  f.Jg = t.Jg;
+  f.Jf = t.Jf;
+  f.Jr = t.Jr;
+  f.Q = t.Q;
+  f.T = t.T;
+  f.Fv = t.Fv;
+  f.S = t.S;
+  f.B = t.B;
+  f.desc = c->d_fdesc;
+  f.n_pairs = c->n_pairs;
+  f.e_pair = c->d_epair;
+  f.terms = c->d_terms;
+  f.status = c->d_status;
+  f.work = c->d_work;
+  f.ws_stride = c->ws_stride;
+  f.counter = c->d_counter;
+  return f;
+}
+
+// Algorithmic work of one full-mode pair: FP64 (factorisation + solves on the
+// 4p + 4 right-hand sides) and the mixable products, in the kernel's order.
+void full_work(double p, double k, double m, double& f64, double& fmix) {
+  const double k2 = k + 2;
+  f64 = m * m * m / 3.0 + 2.0 * (4.0 * p + 4.0) * m * m;
+  fmix = 4 * 2 * p * k * m + 2 * k2 * m * m + 2 * 2 * k2 * k2 * m   // V kernel, projected
+         + 2 * 2 * p * m * m + 6 * 2 * p * p * m                     // geminal kernels
+         + 4 * 2 * p * p * k + 6 * 2 * p * k * k                     // projections, C, R_Q
+         + 2 * k * k * k2 * m + 2 * k * k2 * k2 * m                  // projector term
+         + 2 * 2 * p * p * p;                                        // F R_Q, R_Q F
+}
+
+int tune_full(pf12_ctx* c) {
+  if (c->forced >= 0) {
+    if (c->forced >= pf12::kFullVariants || c->n_ctas_full_v[c->forced] <= 0)
+      return fail(c, PF12_ERR_UNSUPPORTED, "forced variant not available in full mode");
+    c->variant = c->forced;
+    return PF12_OK;
+  }
+  if (c->n_pairs <= c->n_ctas_full_v[0] || c->n_sample == 0) {
+    c->variant = 0;
+    return PF12_OK;
+  }
+  pf12::FullParams f = full_params(c);
+  f.desc = c->d_fdesc_sample;
+  int best = 0;
+  for (int v = 0; v < pf12::kFullVariants; ++v) {
+    if (c->n_ctas_full_v[v] <= 0) continue;
+    f.n_pairs = 1;
+    PF12_CUDA(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->stream));
+    PF12_CUDA(c, pf12::launch_full(f, c->precision, v, 1, c->stream));
+    f.n_pairs = c->n_sample;
+    float ms = 0;
+    PF12_CUDA(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->stream));
+    PF12_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+    PF12_CUDA(c, pf12::launch_full(f, c->precision, v, c->n_ctas_full_v[v], c->stream));
+    PF12_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+    PF12_CUDA(c, cudaEventSynchronize(c->ev[1]));
+    PF12_CUDA(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+    c->tune_ms[v] = ms;
+    if (ms < c->tune_ms[best]) best = v;
+  }
+  c->variant = best;
+  return PF12_OK;
+}
+
+int fit_full(pf12_ctx* c) {
+  if (c->variant < 0) {
+    const int rc = tune_full(c);
+    if (rc != PF12_OK) return rc;
+    c->n_ctas = c->n_ctas_full_v[c->variant];
+  }
+  if (!c->graph_exec) {
+    PF12_CUDA(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->capture_stream);
+    if (e == cudaSuccess)
+      e = pf12::launch_full(full_params(c), c->precision, c->variant, c->n_ctas, c->capture_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "capture full launch");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "end capture");
+    c->graph = g;
+    PF12_CUDA(c, cudaGraphInstantiate(&c->graph_exec, g, 0));
+  }
+  PF12_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+  PF12_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
+  PF12_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+  c->t_fit = true;
+  c->fitted = true;
+  return PF12_OK;
+}
+
+}  // namespace
+
 extern "C" {
+
+int pf12_upload_full(pf12_ctx* c, int32_t n_orb, const int8_t* kind, int64_t n_pairs,
+                     const int32_t* pi, const int32_t* pj, const int32_t* n_pao,
+                     const int32_t* n_pno, const int32_t* n_aux, const pf12_full_tensors* t) {
+  NvtxRange nvtx("pf12_upload_full");
+  if (!c) return PF12_ERR_INVALID_ARG;
+  free_pairs(c);
+  if (n_pairs < 0 || n_orb < 0) return fail(c, PF12_ERR_INVALID_ARG, "negative count");
+  if (c->augment || c->packed)
+    return fail(c, PF12_ERR_UNSUPPORTED, "full mode takes plain PNO spaces and full metrics");
+  if (n_pairs > 0 && (!kind || !pi || !pj || !n_pao || !n_pno || !n_aux || !t))
+    return fail(c, PF12_ERR_INVALID_ARG, "null metadata pointer");
+  if (n_pairs > 0) {
+    const double* ptrs[18] = {t->Ag_i, t->Ag_j, t->Af_i, t->Af_j, t->Ar_i, t->Ar_j,
+                              t->AgF_i, t->AgF_j, t->ArF_i, t->ArF_j, t->Jg, t->Jf, t->Jr,
+                              t->Q, t->T, t->Fv, t->S, t->B};
+    for (const double* q : ptrs)
+      if (!q || !aligned16(q)) return fail(c, PF12_ERR_INVALID_ARG, "tensor pointer null or not 16-byte aligned");
+    if (!t->off_pm || !t->off_mm || !t->off_pk || !t->off_kk || !t->off_pp || !t->off_s || !t->off_b)
+      return fail(c, PF12_ERR_INVALID_ARG, "null offset array");
+  }
+  for (int32_t o = 0; o < n_orb; ++o)
+    if (kind[o] != 0 && kind[o] != 1) return fail(c, PF12_ERR_INVALID_ARG, "orb_kind must be 0 or 1");
+  std::vector<pf12::FullDesc> desc(n_pairs);
+  std::vector<double> cost(n_pairs);
+  double f64 = 0, fmix = 0, bytes = 0;
+  int64_t max_ws = 0;
+  for (int64_t P = 0; P < n_pairs; ++P) {
+    const int32_t i = pi[P], j = pj[P], p = n_pao[P], k = n_pno[P], m = n_aux[P];
+    char buf[160];
+    if (i < 0 || j < 0 || i >= n_orb || j >= n_orb || i > j) {
+      snprintf(buf, sizeof buf, "pair %lld: need 0 <= i <= j < n_orb", (long long)P);
+      return fail(c, PF12_ERR_INVALID_ARG, buf);
+    }
+    if (p < 1 || k < 1 || m < 1 || k > p || m > pf12::kMaxAux || k > pf12::kMaxPno) {
+      snprintf(buf, sizeof buf, "pair %lld: sizes p=%d k=%d m=%d out of range", (long long)P, p, k, m);
+      return fail(c, PF12_ERR_INVALID_ARG, buf);
+    }
+    const int64_t offs[7] = {t->off_pm[P], t->off_mm[P], t->off_pk[P], t->off_kk[P],
+                             t->off_pp[P], t->off_s[P], t->off_b[P]};
+    const int64_t sizes[7] = {(int64_t)(p + 2) * m, (int64_t)m * m, (int64_t)p * k,
+                              (int64_t)k * k, (int64_t)p * p, 2 * (int64_t)k,
+                              (int64_t)k * m * (k + 2)};
+    const int64_t lens[7] = {t->len_pm, t->len_mm, t->len_pk, t->len_kk, t->len_pp, t->len_s,
+                             t->len_b};
+    for (int q = 0; q < 7; ++q)
+      if (offs[q] < 0 || (offs[q] & 1) || offs[q] + sizes[q] > lens[q]) {
+        snprintf(buf, sizeof buf, "pair %lld: offset %d misaligned or block outside its buffer", (long long)P, q);
+        return fail(c, PF12_ERR_INVALID_ARG, buf);
+      }
+    pf12::FullDesc& d = desc[P];
+    d.off_pm = offs[0];
+    d.off_mm = offs[1];
+    d.off_pk = offs[2];
+    d.off_kk = offs[3];
+    d.off_pp = offs[4];
+    d.off_s = offs[5];
+    d.off_b = offs[6];
+    d.p = p;
+    d.k = k;
+    d.m = m;
+    d.pair = (int32_t)P;
+    const int bi = kind[i] == 0, bj = kind[j] == 0;
+    if (i == j) {
+      d.n_ab = (int8_t)bi;
+      d.n_aa = d.n_bb = 0;
+    } else {
+      d.n_ab = (int8_t)(bi + bj);
+      d.n_aa = 1;
+      d.n_bb = (int8_t)(bi * bj);
+    }
+    double c64, cmix;
+    full_work(p, k, m, c64, cmix);
+    cost[P] = c64 + cmix / 8.0;
+    f64 += c64;
+    fmix += cmix;
+    bytes += 8.0 * (10.0 * (p + 2) * m + 3.0 * m * m + (double)p * k + (double)k * k +
+                    (double)p * p + 2.0 * k + (double)k * m * (k + 2));
+    max_ws = std::max(max_ws, pf12::full_slab(p, k, m).total);
+  }
+  std::vector<int64_t> order(n_pairs);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+  std::vector<pf12::FullDesc> sorted(n_pairs);
+  for (int64_t q = 0; q < n_pairs; ++q) sorted[q] = desc[order[q]];
+  const int64_t stride = (max_ws + 31) / 32 * 32;
+  int64_t cap = INT64_MAX;
+  if (c->ws_cap) {
+    cap = (int64_t)(c->ws_cap / 8) / std::max<int64_t>(stride, 1);
+    if (n_pairs > 0 && cap < 1) return fail(c, PF12_ERR_OOM, "workspace_bytes too small for the largest pair");
+  }
+  int64_t want = 1;
+  for (int v = 0; v < pf12::kFullVariants; ++v) {
+    const int bps = pf12::full_blocks_per_sm(c->precision, v);
+    cudaGetLastError();
+    int64_t n_v = std::min<int64_t>(n_pairs, (int64_t)std::max(bps, 0) * c->n_sm);
+    n_v = bps <= 0 ? 0 : std::max<int64_t>(1, std::min(n_v, cap));
+    c->n_ctas_full_v[v] = (int)n_v;
+    want = std::max(want, n_v);
+  }
+  std::vector<pf12::FullDesc> sample;
+  const int64_t n_s = std::min<int64_t>(n_pairs, 4 * want);
+  for (int64_t q = 0; q < n_s; ++q) sample.push_back(sorted[(q * n_pairs) / std::max<int64_t>(n_s, 1)]);
+  const size_t n = (size_t)std::max<int64_t>(n_pairs, 1);
+  cudaError_t e = grow(c->d_fdesc, c->cap_fdesc, n);
+  if (e == cudaSuccess) e = grow(c->d_fdesc_sample, c->cap_fsample, (size_t)std::max<int64_t>(n_s, 1));
+  if (e == cudaSuccess) e = grow(c->d_epair, c->cap_ep, 3 * n);
+  if (e == cudaSuccess) e = grow(c->d_terms, c->cap_terms, (size_t)pf12::kFullTerms * n);
+  if (e == cudaSuccess) e = grow(c->d_status, c->cap_st, n);
+  if (e == cudaSuccess && !c->fixed_allocated) {
+    e = cudaMalloc(&c->d_out3, sizeof(double) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) c->fixed_allocated = true;
+  }
+  if (e == cudaSuccess && n_pairs > 0) e = grow(c->d_work, c->cap_work, (size_t)(want * stride));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_pairs(c);
+    return fail(c, e == cudaErrorMemoryAllocation ? PF12_ERR_OOM : PF12_ERR_CUDA,
+                std::string("device allocation: ") + cudaGetErrorString(e));
+  }
+  if (n_pairs > 0) {
+    PF12_CUDA(c, cudaMemcpyAsync(c->d_fdesc, sorted.data(), sizeof(pf12::FullDesc) * n_pairs,
+                                 cudaMemcpyHostToDevice, c->stream));
+    PF12_CUDA(c, cudaMemcpyAsync(c->d_fdesc_sample, sample.data(), sizeof(pf12::FullDesc) * n_s,
+                                 cudaMemcpyHostToDevice, c->stream));
+  }
+  PF12_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int32_t) * n, c->stream));
+  PF12_CUDA(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t) * 4, c->stream));
+  PF12_CUDA(c, cudaMemsetAsync(c->d_epair, 0, sizeof(double) * 3 * n, c->stream));
+  PF12_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->ft = *t;
+  c->full = true;
+  c->tune_key = "full";     // a later amplitude-only upload never reuses this tuning
+  c->n_pairs = n_pairs;
+  c->n_sample = n_s;
+  c->ws_stride = stride;
+  c->work_bytes = sizeof(double) * (size_t)(want * stride);
+  c->flops64 = f64 + (c->precision == PF12_FP64 ? fmix : 0.0);
+  c->flops_mix = fmix;
+  c->bytes_in = bytes;
+  c->n_ctas = c->n_ctas_full_v[0];
+  for (int v = 0; v < pf12::kFwdVariants; ++v) c->n_ctas_v[v] = v < pf12::kFullVariants ? c->n_ctas_full_v[v] : 0;
+  c->uploaded = true;
+  return PF12_OK;
+}
+
+int pf12_full_terms(pf12_ctx* c, double* terms_dev) {
+  if (!c || !terms_dev) return fail(c, PF12_ERR_INVALID_ARG, "null argument");
+  if (!c->full) return fail(c, PF12_ERR_INVALID_ARG, "pf12_full_terms needs pf12_upload_full");
+  if (!c->fitted) return fail(c, PF12_ERR_INVALID_ARG, "pf12_full_terms before pf12_fit");
+  if (c->n_pairs == 0) return PF12_OK;
+  PF12_CUDA(c, cudaMemcpyAsync(terms_dev, c->d_terms, sizeof(double) * pf12::kFullTerms * c->n_pairs,
+                               cudaMemcpyDeviceToDevice, c->stream));
+  return PF12_OK;
+}
 
 int pf12_set_arrival(pf12_ctx* c, int32_t n_groups, const int64_t* group_end,
                      const uint32_t* ready_dev, uint32_t epoch) {
   if (!c) return PF12_ERR_INVALID_ARG;
   if (!c->uploaded) return fail(c, PF12_ERR_INVALID_ARG, "pf12_set_arrival before pf12_upload_pairs");
+  if (c->full) return fail(c, PF12_ERR_UNSUPPORTED, "streamed inputs are not offered in full mode");
   if (n_groups == 0 || c->n_pairs == 0) {
     const bool was = c->arr_ready != nullptr;
     c->arr_ready = nullptr;
@@ -801,6 +1079,7 @@ int pf12_fit(pf12_ctx* c) {
     c->fitted = true;
     return PF12_OK;
   }
+  if (c->full) return fit_full(c);
   if (c->arr_dirty) {
     const int rc = apply_queue_order(c);
     if (rc != PF12_OK) return rc;
@@ -849,6 +1128,7 @@ int pf12_fit(pf12_ctx* c) {
 
 int pf12_build_v(pf12_ctx* c, double* V_dev) {
   if (!c || !V_dev) return fail(c, PF12_ERR_INVALID_ARG, "null argument");
+  if (c->full) return fail(c, PF12_ERR_UNSUPPORTED, "full mode keeps no V (use pf12_full_terms)");
   if (!c->fitted) return fail(c, PF12_ERR_INVALID_ARG, "pf12_build_v before pf12_fit");
   if (c->n_pairs == 0) return PF12_OK;
   for (int64_t P = 0; P < c->n_pairs; ++P) {
@@ -962,6 +1242,7 @@ int pf12_backward(pf12_ctx* c, double dE, double* dAgi, double* dAgj, double* dA
                   double* dQ, double* dT) {
   NvtxRange nvtx("pf12_backward");
   if (!c) return PF12_ERR_INVALID_ARG;
+  if (c->full) return fail(c, PF12_ERR_UNSUPPORTED, "no adjoint of the full pair energy");
   if (!c->uploaded) return fail(c, PF12_ERR_INVALID_ARG, "pf12_backward before pf12_upload_pairs");
   if (c->gather) return fail(c, PF12_ERR_INVALID_ARG, "gather mode: use pf12_backward_gather");
   if (c->n_pairs == 0) return PF12_OK;
@@ -995,6 +1276,7 @@ int pf12_backward(pf12_ctx* c, double dE, double* dAgi, double* dAgj, double* dA
 int pf12_backward_gather(pf12_ctx* c, double dE, double* dBg, double* dBf, double* dQ, double* dT) {
   NvtxRange nvtx("pf12_backward_gather");
   if (!c) return PF12_ERR_INVALID_ARG;
+  if (c->full) return fail(c, PF12_ERR_UNSUPPORTED, "no adjoint of the full pair energy");
   if (!c->uploaded || !c->gather)
     return fail(c, PF12_ERR_INVALID_ARG, "pf12_backward_gather needs pf12_upload_pairs_gather");
   if (c->n_pairs == 0) return PF12_OK;

@@ -75,6 +75,90 @@ struct BwdParams {
   double *dAgi, *dAgj, *dAfi, *dAfj, *dQ, *dT;
 };
 
+// Complete pair energy (full mode): every term of E_(2)F12 per pair.  Factor
+// blocks are (p + 2) x m (PAO rows, then the occupied i, j); see
+// pf12_full_tensors in include/pairf12.h for the inputs.
+struct FullDesc {
+  int64_t off_pm, off_mm, off_pk, off_kk, off_pp, off_s, off_b;
+  int32_t p, k, m, pair;
+  int8_t n_ab, n_aa, n_bb, pad_;
+  int32_t pad2_;
+};
+static_assert(sizeof(FullDesc) == 80, "FullDesc layout");
+
+constexpr int kFullTerms = 14;   // spatial terms per pair (order of oracle TERM_NAMES)
+constexpr int kFullChunk = 128;  // auxiliary functions per chunk of the projector term
+
+struct FullParams {
+  const double *Agi, *Agj, *Afi, *Afj, *Ari, *Arj, *AgiF, *AgjF, *AriF, *ArjF;
+  const double *Jg, *Jf, *Jr, *Q, *T, *Fv, *S, *B;
+  const FullDesc* desc;
+  int64_t n_pairs;
+  double* e_pair;     // n_pairs x 3, caller's index
+  double* terms;      // n_pairs x kFullTerms, caller's index
+  int32_t* status;    // n_pairs, caller's index
+  double* work;       // n_ctas * ws_stride doubles
+  int64_t ws_stride;
+  int32_t* counter;   // work-queue head
+};
+
+// Slab of one full-mode pair (doubles): offsets of its regions, ld = m rounded
+// up to 4, lq = p rounded up to 4.
+struct FullSlab {
+  int64_t M, W1, W2, Atfi, Atfj, Cti, Ctj, KR, KRiF, KRjF, RQ, S1, S2, Y, Zt, FvQ, Ft, U,
+      Rpno, QtFQ, Cm, Vh, H, total;
+};
+inline __host__ __device__ int64_t slab_take(int64_t& o, int64_t n) {
+  const int64_t at = o;
+  o += (n + 31) / 32 * 32;   // every region starts on 256 bytes
+  return at;
+}
+inline __host__ __device__ FullSlab full_slab(int p, int k, int m) {
+  const int64_t ld = (m + 3) / 4 * 4, lq = (p + 3) / 4 * 4, k2 = k + 2;
+  FullSlab s{};
+  int64_t o = 0;
+#define take(n) slab_take(o, (n))
+  s.M = take((int64_t)(m + 4 * p + 4) * ld);
+  s.W1 = take((int64_t)p * ld);
+  s.W2 = take((int64_t)p * ld);
+  s.Atfi = take(k2 * ld);
+  s.Atfj = take(k2 * ld);
+  s.Cti = take(k2 * ld);
+  s.Ctj = take(k2 * ld);
+  s.KR = take((int64_t)p * lq);
+  s.KRiF = take((int64_t)p * lq);
+  s.KRjF = take((int64_t)p * lq);
+  s.RQ = take((int64_t)p * lq);
+  s.S1 = take((int64_t)p * lq);
+  s.S2 = take((int64_t)p * lq);
+  s.Y = take((int64_t)p * k);
+  s.Zt = take((int64_t)p * k);
+  s.FvQ = take((int64_t)p * k);
+  s.Ft = take((int64_t)p * k);
+  s.U = take((int64_t)p * k);
+  s.Rpno = take((int64_t)k * k);
+  s.QtFQ = take((int64_t)k * k);
+  s.Cm = take((int64_t)k * k);
+  s.Vh = take(k2 * k2);
+  s.H = take((int64_t)k * kFullChunk * k2);
+#undef take
+  s.total = o + 64;
+  return s;
+}
+
+constexpr int kFullVariants = 2;   // 2 / 3 CTAs per SM
+cudaError_t launch_full(const FullParams& prm, int precision, int variant, int n_ctas,
+                        cudaStream_t s);
+int full_blocks_per_sm(int precision, int variant);
+cudaError_t launch_full_f64_2(const FullParams& prm, int n_ctas, cudaStream_t s);
+cudaError_t launch_full_f64_3(const FullParams& prm, int n_ctas, cudaStream_t s);
+cudaError_t launch_full_f32_2(const FullParams& prm, int n_ctas, cudaStream_t s);
+cudaError_t launch_full_f32_3(const FullParams& prm, int n_ctas, cudaStream_t s);
+int occupancy_full_f64_2();
+int occupancy_full_f64_3();
+int occupancy_full_f32_2();
+int occupancy_full_f32_3();
+
 // per-CTA workspace (doubles) for a pair of sizes (p, k, m), forward / backward
 inline int64_t ld_of(int m) { return (int64_t)((m + 3) / 4 * 4); }
 // offset of the sieved A blocks (4 x p x m) inside a forward slab

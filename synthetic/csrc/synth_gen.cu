@@ -123,9 +123,110 @@ __global__ void __launch_bounds__(256) metric_kernel(const PairMeta* meta, const
     }
 }
 
+// Full-energy inputs (synthetic/full.py).  One block row per pair.
+struct FullMeta {
+  int64_t dst, src;  // element offsets (src: the block being Fock-transformed)
+  int32_t p, k, m, key;
+  int32_t tid, tid2, tid3, canon;
+  double scale, eps;
+};
+
+// Fock-transformed occupied factors: dst[e] = fl(fl(eps src[e]) + fl(z(e) scale)),
+// e < p m (the PAO rows); scale = 0 in the canonical limit
+__global__ void fill_focktrans_kernel(const FullMeta* meta, uint32_t seed, const double* src,
+                                      double* dst) {
+  const FullMeta fm = meta[blockIdx.y];
+  const int64_t total = (int64_t)fm.p * fm.m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 w = philox((uint32_t)(e >> 1), 0u, (uint32_t)fm.key, (uint32_t)fm.tid, seed, kKeyHi);
+    const int z = (e & 1) ? ih16(w.z, w.w) : ih16(w.x, w.y);
+    const double n = fm.canon ? 0.0 : __dmul_rn((double)z, fm.scale);
+    dst[fm.dst + e] = __dadd_rn(__dmul_rn(fm.eps, src[fm.src + e]), n);
+  }
+}
+
+// Virtual Fock block (p x p, symmetric): diagonal 0.5 + 2.5 u (u the low 20
+// bits of word 0 of call (r, 1) times 2^-20), off-diagonal element (r, c) the
+// Gaussian of stream element min(r, c) p + max(r, c); canonical: 1.5 I
+__global__ void fill_fock_virtual_kernel(const FullMeta* meta, uint32_t seed, double* out) {
+  const FullMeta fm = meta[blockIdx.y];
+  const int p = fm.p;
+  const int64_t total = (int64_t)p * p;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / p), c = (int)(e - (int64_t)r * p);
+    double v;
+    if (fm.canon) {
+      v = r == c ? 1.5 : 0.0;
+    } else if (r == c) {
+      const uint4 w = philox((uint32_t)r, 1u, (uint32_t)fm.key, (uint32_t)fm.tid, seed, kKeyHi);
+      const double u = (double)(w.x & 0xFFFFFu) * 0x1p-20;
+      v = __dadd_rn(0.5, __dmul_rn(2.5, u));
+    } else {
+      const int64_t se = (int64_t)min(r, c) * p + max(r, c);
+      const uint4 w = philox((uint32_t)(se >> 1), 0u, (uint32_t)fm.key, (uint32_t)fm.tid, seed, kKeyHi);
+      const int z = (se & 1) ? ih16(w.z, w.w) : ih16(w.x, w.y);
+      v = __dmul_rn((double)z, fm.scale);
+    }
+    out[fm.dst + e] = v;
+  }
+}
+
+// PNO-pair factors (k x m x (k + 2)): element (c, X, q), q < k, is stream
+// (tid) element (min(c, q) m + X)(k + 2) + max(c, q); q = k the element c m + X
+// of stream tid2, q = k + 1 of stream tid3
+__global__ void fill_pno_pair_kernel(const FullMeta* meta, uint32_t seed, double* out) {
+  const FullMeta fm = meta[blockIdx.y];
+  const int k = fm.k, m = fm.m, k2 = k + 2;
+  const int64_t total = (int64_t)k * m * k2;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(e % k2);
+    const int64_t cx = e / k2;
+    const int X = (int)(cx % m), c = (int)(cx / m);
+    int64_t se;
+    int tid;
+    if (q < k) {
+      se = ((int64_t)min(c, q) * m + X) * k2 + max(c, q);
+      tid = fm.tid;
+    } else {
+      se = (int64_t)c * m + X;
+      tid = q == k ? fm.tid2 : fm.tid3;
+    }
+    const uint4 w = philox((uint32_t)(se >> 1), 0u, (uint32_t)fm.key, (uint32_t)tid, seed, kKeyHi);
+    const int z = (se & 1) ? ih16(w.z, w.w) : ih16(w.x, w.y);
+    out[fm.dst + e] = __dmul_rn((double)z, fm.scale);
+  }
+}
+
+enum { kFullFockTrans = 0, kFullFockVirtual = 1, kFullPnoPair = 2 };
+
 }  // namespace
 
 extern "C" {
+
+// Full-energy inputs: kind 0 = Fock-transformed factors (src, dst buffers),
+// 1 = virtual Fock blocks, 2 = PNO-pair factors (dst buffer only).
+int synth_fill_full(int kind, int n, const void* meta_host, uint32_t seed, const double* src,
+                    double* dst, void* stream) {
+  if (n <= 0) return 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  FullMeta* d = nullptr;
+  if (cudaMalloc(&d, sizeof(FullMeta) * n) != cudaSuccess) return -3;
+  cudaMemcpyAsync(d, meta_host, sizeof(FullMeta) * n, cudaMemcpyHostToDevice, s);
+  for (int b = 0; b < n; b += 65535) {
+    const int nb = n - b < 65535 ? n - b : 65535;
+    const dim3 grid(64, nb);
+    if (kind == kFullFockTrans) fill_focktrans_kernel<<<grid, 256, 0, s>>>(d + b, seed, src, dst);
+    else if (kind == kFullFockVirtual) fill_fock_virtual_kernel<<<grid, 256, 0, s>>>(d + b, seed, dst);
+    else fill_pno_pair_kernel<<<grid, 256, 0, s>>>(d + b, seed, dst);
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
 
 // Fill n blocks; meta (host, n entries of {off, rows, cols, key, tid, scale}).
 int synth_fill_gauss16(int n, const void* meta_host, uint32_t seed, double* out, void* stream) {

@@ -44,7 +44,8 @@ from .philox import philox4x32
  TID_ARI, TID_ARJ, TID_XR, TID_NGIF, TID_NGJF, TID_NRIF, TID_NRJF,
  TID_FV, TID_S_I, TID_S_J, TID_B, TID_B_I, TID_B_J, TID_EPS) = range(9, 29)
 
-R_SCALE = 2.0 ** -8    # geminal operator scale: its factors and its metric (exact power of 2)
+R_SCALE = 2.0 ** -12   # geminal operator scale: its factors and its metric (exact power of 2)
+OCC_SCALE = 0.25       # occupied rows (ii|X), (jj|X), (ij|X) relative to the PAO rows
 FOCK_NOISE = 0.0625    # couplings of i_F to the other occupied orbitals
 FV_OFFDIAG = 0.03125   # off-diagonal virtual Fock couplings
 SINGLES_STD = 5e-3
@@ -104,11 +105,13 @@ def full_pair_inputs(wl, P, eps=None):
     c = W.factor_scale(wl.decay[P])
     out = {}
 
+    co = c * OCC_SCALE
+
     def occ_rows(tii, tjj, tij):
-        ii = W._gauss16(wl.seed, key, tii, m, c)
+        ii = W._gauss16(wl.seed, key, tii, m, co)
         if diag:
             return ii, ii, ii
-        return ii, W._gauss16(wl.seed, key, tjj, m, c), W._gauss16(wl.seed, key, tij, m, c)
+        return ii, W._gauss16(wl.seed, key, tjj, m, co), W._gauss16(wl.seed, key, tij, m, co)
 
     for x, tids in (("g", (TID_OCCG_II, TID_OCCG_JJ, TID_OCCG_IJ)),
                     ("f", (TID_OCCF_II, TID_OCCF_JJ, TID_OCCF_IJ))):
