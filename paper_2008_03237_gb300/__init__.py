@@ -210,6 +210,7 @@ class PairF12:
             *[_ptr(a, ctypes.c_int32) for a in meta], ctypes.byref(ft)))
         self._keep = (tensors, offs, meta, kind)
         self.n_pairs = n
+        self.len_kk = tensors["T"].numel()
 
     def full_terms(self, terms=None):
         """Per-pair spatial terms of the last full-mode fit (n_pairs x 14)."""
