@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint figure (C40H81)")
+    ap.add_argument("--no-full", action="store_true",
+                    help="skip the complete-pair-energy figure (C40H81)")
     ap.add_argument("--shard", action="store_true",
                     help="torchrun: split ONE pair list over the ranks (LPT) and gather the pair "
                          "energies in list order every step (strong scaling); default: every "
@@ -444,6 +446,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.empty_cache()
     if not args.no_adjoint and world == 1:
         out["adjoint"] = run_adjoint(args, pf, torch, device)
+    if not args.no_full and world == 1:
+        out["full_energy"] = full_energy_figure(args, pf, torch, device, "c40h81", steps=3, warmup=1)
     out["fp64_probe"] = fp64_probe()
     return wl, f64, fmix, byts, out
 
@@ -491,22 +495,38 @@ class _Null:
         return False
 
 
+def host_memory_available():
+    """Bytes the host can still give (MemAvailable of /proc/meminfo), or 0."""
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
 def run_e2e(args, wl_full, t_full, lay_full, pf, torch):
-    """Pairs/s of a bounded prefix of the workload whose packed inputs (<= 48 GB)
-    sit in pinned host memory: every step uploads the pair list, copies the
-    inputs host->device group by group on a copy stream while one persistent
-    fit (launched at once) waits for each group's arrival flag, and reads the
-    total and the pair statuses back to the host."""
+    """Pairs/s of the workload end to end from pinned host memory: every step
+    uploads the pair list, copies the inputs host->device group by group on a
+    copy stream while one persistent fit (launched at once) waits for each
+    group's arrival flag, and reads the total and the pair statuses back to
+    the host.  The whole list is used when its packed inputs fit in 70 % of
+    the host's available memory, else the longest prefix that does (recorded
+    in the result).  The resident device inputs are released once the host
+    copies exist (t_full is emptied)."""
     import synthetic as S
     from synthetic import workloads as W
-    budget = 48e9
+    budget = 0.7 * host_memory_available()
     n = 0
     acc = 0.0
     p, k, m = wl_full.n_pao, wl_full.n_pno, wl_full.n_aux
-    per = 8.0 * (4 * p * m + 2 * m * m + p * k + k * k)
+    per = 8.0 * (4 * p * m + m * (m + 1) + p * k + k * k)      # packed metric triangles
     while n < wl_full.n_pairs and acc + per[n] <= budget:
         acc += per[n]
         n += 1
+    if n == 0:
+        raise RuntimeError("no host memory for the end-to-end inputs")
     prefix = wl_full.subset(np.arange(n))
     lay_src = W.packed_offsets(prefix)        # where the prefix blocks sit in t_full
     # the host keeps its pair list longest first (the library's cost model), so
@@ -515,7 +535,8 @@ def run_e2e(args, wl_full, t_full, lay_full, pf, torch):
     pp, kk, mm_ = (prefix.n_pao.astype(float), prefix.n_pno.astype(float), prefix.n_aux.astype(float))
     cost = mm_ ** 3 / 3 + 4 * kk * mm_ ** 2 + (8 * pp * kk * mm_ + 2 * kk * mm_ ** 2 + 4 * kk * kk * mm_) / 8
     order = np.argsort(-cost, kind="stable")
-    wl = prefix.subset(order, name=f"{wl_full.name}[first {n} pairs, longest first]")
+    label = "all" if n == wl_full.n_pairs else f"first {n}"
+    wl = prefix.subset(order, name=f"{wl_full.name}[{label} pairs, longest first]")
     # and the metrics as packed lower triangles (pf12_opts.metric_packed): they
     # are symmetric, and that cuts the bytes each step copies by a third
     lay = W.packed_offsets(wl, metric_packed=True)
@@ -542,8 +563,11 @@ def run_e2e(args, wl_full, t_full, lay_full, pf, torch):
                 z = int(size[kx][P])
                 src[o_d:o_d + z] = t_full[x][o_s:o_s + z]
         host[x] = torch.empty(max(L, 2), dtype=torch.float64, pin_memory=True)
-        host[x].copy_(src.cpu())
+        host[x].copy_(src)
         del src
+    del tril
+    t_full.clear()                  # the resident inputs are not needed any more
+    torch.cuda.empty_cache()
     h2d = sum(v.numel() * 8 for v in host.values())
     from paper_2008_03237_gb300.stream import HostStreamer
     # raw pinned host -> device bandwidth of this machine (one large copy)
@@ -578,6 +602,7 @@ def run_e2e(args, wl_full, t_full, lay_full, pf, torch):
     torch.cuda.empty_cache()
     return {"value": n / dt, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": 32 + 4 * n, "pairs": n, "ms_per_step": dt * 1e3,
+            "host_budget_gb": budget / 1e9,
             "workload": wl.name, "arrival_groups": nb, "h2d_gbs_raw": h2d_gbs,
             "metric_layout": "packed lower triangles",
             "note": "pinned host inputs copied in growing groups (0.5 GB doubling to 4 GB) on a "
@@ -653,7 +678,7 @@ def main():
                       "sample_ms": o["stats"]["tune_ms"],
                       "ctas": o["stats"]["ctas_variant"]},
     }
-    for key in ("fp64_mode", "error_vs_fp64", "e2e", "adjoint"):
+    for key in ("fp64_mode", "error_vs_fp64", "e2e", "adjoint", "full_energy"):
         if key in o:
             line[key] = o[key]
     if args.backward:
@@ -692,10 +717,74 @@ def full_flops(wl):
     return f64, fmix, byts
 
 
+def full_energy_figure(args, pf, torch, device, name, max_pairs=0, local_rank=0, steps=None,
+                       warmup=None, sample_clocks=False):
+    """The complete pair energy on one workload with resident inputs: the
+    requested precision timed (CUDA events around fit + energy), the FP64
+    mode beside it, and the error of the mixed energies against FP64 on the
+    chemical scale."""
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    wl = make_workload(name, max_pairs)
+    f64, fmix, byts = full_flops(wl)
+    t, lay = device.allocate_full(wl)
+    device.fill_full(wl, t, lay)
+    res = {}
+    for prec in (args.precision, "fp64") if args.precision != "fp64" else ("fp64",):
+        eng = pf.PairF12(prec, variant=args.variant if args.full else None)
+        eng.upload_full(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
+        n_steps = steps if prec == args.precision else max(2, steps // 2)
+        for _ in range(warmup if prec == args.precision else 1):
+            eng.fit()
+            eng.energy(want_host=False)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local_rank) if (sample_clocks and prec == args.precision) else _Null()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with sampler:
+            ev0.record()
+            for _ in range(n_steps):
+                eng.fit()
+                eng.energy(want_host=False)
+            ev1.record()
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / n_steps
+        E, e = eng.energy()
+        st = eng.stats()
+        res[prec] = {"ms": ms, "ms_fit": st["ms_fit"], "E": E, "e": e.cpu().numpy(),
+                     "bad": int((eng.pair_status() != 0).sum()), "variant": st["tile_config"],
+                     "tune_ms": st["tune_ms"][:2],
+                     "clocks": sampler.summary() if isinstance(sampler, ClockSampler) else None}
+        eng.close()
+    del t
+    torch.cuda.empty_cache()
+    head = res[args.precision]
+    achieved = (f64 + (fmix if args.precision == "fp64" else 0)) / head["ms_fit"] / 1e9
+    out = {"workload": wl.name, "pairs": wl.n_pairs, "precision": args.precision,
+           "energy": "complete E_(2)F12 per pair (occupied, amplitude, C and singles terms of "
+                     "Vtilde; B~ with i_F, j_F; PNO projector term)",
+           "value": wl.n_pairs / head["ms"] * 1e3, "unit": "pairs/s", "ms_per_step": head["ms"],
+           "kernel": "pair_full_kernel (fused persistent)", "ms_per_launch": head["ms_fit"],
+           "fp64_tflops": f64 / head["ms_fit"] / 1e9, "mixed_part_tflops": fmix / head["ms_fit"] / 1e9,
+           "achieved_tflops": achieved, "frac_of_fp64_peak": achieved / FP64_PEAK_TFLOPS,
+           "inputs_gb": byts / 1e9, "E_total_raw": head["E"], "pairs_failed": head["bad"],
+           "variant": head["variant"], "tune_ms": head["tune_ms"], "clocks": head["clocks"]}
+    if "fp64" in res and args.precision != "fp64":
+        r64 = res["fp64"]
+        sum_abs = float(np.abs(r64["e"].sum(axis=1)).sum())
+        kappa = CHEM_SCALE_PER_ORB * wl.n_orb / sum_abs
+        out["fp64_mode"] = {"value": wl.n_pairs / r64["ms"] * 1e3, "ms_per_step": r64["ms"],
+                            "fp64_tflops": (f64 + fmix) / r64["ms_fit"] / 1e9,
+                            "frac_of_fp64_peak": (f64 + fmix) / r64["ms_fit"] / 1e9 / FP64_PEAK_TFLOPS}
+        out["error_vs_fp64"] = {"total_Eh_normalised": abs(head["E"] - r64["E"]) * kappa,
+                                "max_pair_Eh_normalised": float(np.abs(head["e"] - r64["e"]).max() * kappa),
+                                "kappa": kappa}
+    return out
+
+
 def run_full(args, rank, world, local_rank):
-    """The complete pair energy on one workload (default C40H81, whose inputs
-    stay resident): mixed precision timed as the headline, the FP64 mode beside
-    it, and the error of the mixed energies against FP64 on the chemical scale."""
+    """bench.py --full: the complete pair energy as the headline line (default
+    workload C40H81, whose inputs stay resident)."""
     import torch
 
     import __graft_entry__
@@ -704,67 +793,28 @@ def run_full(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     __graft_entry__.build()
     name = args.workload if args.workload != "c160h321" or args.max_pairs else "c40h81"
-    wl = make_workload(name, args.max_pairs, rank)
-    f64, fmix, byts = full_flops(wl)
-    t, lay = device.allocate_full(wl)
-    device.fill_full(wl, t, lay)
-    res = {}
-    for prec in (args.precision, "fp64") if args.precision != "fp64" else ("fp64",):
-        eng = pf.PairF12(prec, variant=args.variant)
-        eng.upload_full(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
-        steps = args.steps if prec == args.precision else max(2, args.steps // 2)
-        for _ in range(args.warmup if prec == args.precision else 1):
-            eng.fit()
-            eng.energy(want_host=False)
-        torch.cuda.synchronize()
-        sampler = ClockSampler(local_rank) if prec == args.precision else _Null()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        with sampler:
-            ev0.record()
-            for _ in range(steps):
-                eng.fit()
-                eng.energy(want_host=False)
-            ev1.record()
-            torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1) / steps
-        E, e = eng.energy()
-        st = eng.stats()
-        res[prec] = {"ms": ms, "ms_fit": st["ms_fit"], "E": E, "e": e.cpu().numpy(),
-                     "bad": int((eng.pair_status() != 0).sum()), "variant": st["tile_config"],
-                     "tune_ms": st["tune_ms"][:2],
-                     "clocks": sampler.summary() if prec == args.precision else None}
-        eng.close()
-    head = res[args.precision]
-    line = {"metric": METRIC, "value": wl.n_pairs / head["ms"] * 1e3, "unit": "pairs/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"],
+    fig = full_energy_figure(args, pf, torch, device, name, args.max_pairs, local_rank,
+                             sample_clocks=True)
+    line = {"metric": METRIC, "value": fig["value"], "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": fig["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64+f32" if args.precision != "fp64" else "f64",
             "data": "synthetic (seeded Philox4x32-10 draws, device-resident)",
-            "config": {"workload": wl.name, "pairs": wl.n_pairs, "precision": args.precision,
-                       "energy": "complete E_(2)F12 per pair (occupied, amplitude, C and singles "
-                                 "terms of Vtilde; B~ with i_F, j_F; PNO projector term)",
-                       "l2": f"inputs {byts / 1e9:.0f} GB >> 129 MB L2, no flush"},
-            "tflops": {"fp64": f64 / head["ms_fit"] / 1e9, "mixed_part": fmix / head["ms_fit"] / 1e9},
-            "roofline": {"bound": "alu", "achieved": (f64 + (fmix if args.precision == "fp64" else 0))
-                         / head["ms_fit"] / 1e9, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "kernel": "pair_full_kernel (fused persistent)",
-                         "ms_per_launch": head["ms_fit"], "traffic": None},
-            "clocks": head["clocks"], "gpu_launches": 2 * args.steps, "e2e": None,
-            "E_total_raw": head["E"], "pairs_failed": head["bad"],
-            "autotuner": {"variant": head["variant"], "sample_ms": head["tune_ms"],
+            "config": {"workload": fig["workload"], "pairs": fig["pairs"],
+                       "precision": args.precision, "energy": fig["energy"],
+                       "l2": f"inputs {fig['inputs_gb']:.0f} GB >> 129 MB L2, no flush"},
+            "tflops": {"fp64": fig["fp64_tflops"], "mixed_part": fig["mixed_part_tflops"]},
+            "roofline": {"bound": "alu", "achieved": fig["achieved_tflops"],
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": fig["frac_of_fp64_peak"], "kernel": fig["kernel"],
+                         "ms_per_launch": fig["ms_per_launch"], "traffic": None},
+            "clocks": fig["clocks"], "gpu_launches": 2 * args.steps, "e2e": None,
+            "E_total_raw": fig["E_total_raw"], "pairs_failed": fig["pairs_failed"],
+            "autotuner": {"variant": fig["variant"], "sample_ms": fig["tune_ms"],
                           "variants": ["2 CTAs/SM", "3 CTAs/SM"]}}
-    line["roofline"]["frac"] = line["roofline"]["achieved"] / FP64_PEAK_TFLOPS
-    if "fp64" in res and args.precision != "fp64":
-        r64 = res["fp64"]
-        sum_abs = float(np.abs(r64["e"].sum(axis=1)).sum())
-        kappa = CHEM_SCALE_PER_ORB * wl.n_orb / sum_abs
-        line["fp64_mode"] = {"value": wl.n_pairs / r64["ms"] * 1e3, "ms_per_step": r64["ms"],
-                             "fp64_tflops": (f64 + fmix) / r64["ms_fit"] / 1e9,
-                             "frac_of_fp64_peak": (f64 + fmix) / r64["ms_fit"] / 1e9 / FP64_PEAK_TFLOPS}
-        line["error_vs_fp64"] = {"total_Eh_normalised": abs(head["E"] - r64["E"]) * kappa,
-                                 "max_pair_Eh_normalised": float(np.abs(head["e"] - r64["e"]).max() * kappa),
-                                 "kappa": kappa}
+    for key in ("fp64_mode", "error_vs_fp64"):
+        if key in fig:
+            line[key] = fig[key]
     if rank == 0:
         print(json.dumps(line), flush=True)
 
