@@ -674,9 +674,13 @@ def main():
         "gpu_launches": 2 * args.steps,
         "E_total_raw": o["E"], "pairs_failed": o["status_bad"],
         "autotuner": {"variant": o["stats"]["tile_config"],
-                      "variants": ["SIMT 2 CTAs/SM", "SIMT 3 CTAs/SM", "tcgen05 3 CTAs/SM"],
-                      "sample_ms": o["stats"]["tune_ms"],
-                      "ctas": o["stats"]["ctas_variant"]},
+                      "variants": ["SIMT 2 CTAs/SM look-ahead 8", "SIMT 3 CTAs/SM look-ahead 8",
+                                   "tcgen05 3 CTAs/SM look-ahead 8", "SIMT 3 CTAs/SM look-ahead 16"],
+                      "sample_ms_median_of_3": o["stats"]["tune_ms"],
+                      "ctas": o["stats"]["ctas_variant"],
+                      "tile_shape": {n: o["stats"][n] for n in ("look_depth", "ctas_per_sm",
+                                                                 "tensor_cores", "gemm_tile",
+                                                                 "gemm_k_chunk", "panel_width")}},
     }
     for key in ("fp64_mode", "error_vs_fp64", "e2e", "adjoint", "full_energy"):
         if key in o:

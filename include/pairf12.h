@@ -144,13 +144,23 @@ typedef struct {
   int32_t n_ctas;        /* persistent CTAs of the fused pair kernel */
   int32_t launches_fit;  /* kernels launched by one pf12_fit */
   int32_t tile_config;   /* autotuner choice: forward variant (0: SIMT, 2 CTAs/SM; 1: SIMT,
-                            3 CTAs/SM; 2: tcgen05 tensor-core contractions, mixed mode only) */
+                            3 CTAs/SM; 2: tcgen05 tensor-core contractions, mixed mode only;
+                            3: SIMT, 3 CTAs/SM, Cholesky look-ahead 16; full mode: 0 / 1 =
+                            2 / 3 CTAs/SM); its tile shape is reported below */
   int32_t graph_used;    /* 1 when pf12_fit replays a captured CUDA graph */
-  double tune_ms[3];     /* autotuner timings of the variants on its sample (0 if not run) */
-  int32_t ctas_variant[3]; /* persistent CTAs each variant launches (0: unavailable) */
+  double tune_ms[4];     /* autotuner timings of the variants on its sample, median of three
+                            launches (0 if not run or unavailable) */
+  int32_t ctas_variant[4]; /* persistent CTAs each variant launches (0: unavailable) */
   int32_t bwd_variant;   /* adjoint variant (0: 2 CTAs/SM, 1: 3 CTAs/SM; -1 before tuning) */
   int32_t sieve_tma;     /* gather mode: 1 when the sieve uses TMA tile::gather4 loads */
   double tune_bwd_ms[2]; /* adjoint tuner timings */
+  /* tile shape of the chosen forward variant */
+  int32_t look_depth;    /* Cholesky panels per look-ahead group (deep update every 32 x this) */
+  int32_t ctas_per_sm;   /* resident persistent CTAs per SM */
+  int32_t tensor_cores;  /* 1: projections and the J_f product on tcgen05 */
+  int32_t gemm_tile;     /* output tile edge of the CTA GEMM */
+  int32_t gemm_k_chunk;  /* K chunk staged per step of the CTA GEMM */
+  int32_t panel_width;   /* Cholesky / solve panel width */
 } pf12_stats_t;
 
 /* Create a context.  opts may be NULL (FP64, legacy stream, no cap). */

@@ -57,9 +57,12 @@ class Stats(ctypes.Structure):
                 ("flops_mixed", ctypes.c_double), ("bytes_in", ctypes.c_double),
                 ("n_pairs", ctypes.c_int64), ("n_ctas", ctypes.c_int32),
                 ("launches_fit", ctypes.c_int32), ("tile_config", ctypes.c_int32),
-                ("graph_used", ctypes.c_int32), ("tune_ms", ctypes.c_double * 3),
-                ("ctas_variant", ctypes.c_int32 * 3), ("bwd_variant", ctypes.c_int32),
-                ("sieve_tma", ctypes.c_int32), ("tune_bwd_ms", ctypes.c_double * 2)]
+                ("graph_used", ctypes.c_int32), ("tune_ms", ctypes.c_double * 4),
+                ("ctas_variant", ctypes.c_int32 * 4), ("bwd_variant", ctypes.c_int32),
+                ("sieve_tma", ctypes.c_int32), ("tune_bwd_ms", ctypes.c_double * 2),
+                ("look_depth", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("tensor_cores", ctypes.c_int32), ("gemm_tile", ctypes.c_int32),
+                ("gemm_k_chunk", ctypes.c_int32), ("panel_width", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); the same names as the C entry points

@@ -220,14 +220,16 @@ __device__ __forceinline__ void cta_gemm(int M, int N, int K, const double* A, i
 // scratch.  Returns false on every thread when a pivot is not positive and
 // finite (J_g not SPD).
 //
-// Panels are kNB = 32 wide and grouped kLook = 8 at a time: inside a group each
-// panel is first brought up to date by the group's earlier panels (a narrow
-// left-looking update), then factored (warp-level diagonal block, in-register
-// panel solve); the columns right of the group get one update of depth
-// kLook * 32 = 256.  The trailing matrix is thus read and written once per
-// group instead of once per panel; the flop count is unchanged.
+// Panels are kNB = 32 wide and grouped LOOK at a time (8 by default; the
+// autotuner also tries 16): inside a group each panel is first brought up to
+// date by the group's earlier panels (a narrow left-looking update), then
+// factored (warp-level diagonal block, in-register panel solve); the columns
+// right of the group get one update of depth LOOK * 32.  The trailing matrix
+// is thus read and written once per group instead of once per panel; the flop
+// count is unchanged.
 constexpr int kLook = 8;
 
+template <int kLook = pf12::kLook>
 __device__ __forceinline__ bool chol_augmented(double* M, int64_t ld, int m, int rows,
                                                CholSmem& cs, GemmSmem& gs) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

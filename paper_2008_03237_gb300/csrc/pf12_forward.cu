@@ -13,17 +13,21 @@
 
 namespace pf12 {
 
-// Forward variants the autotuner chooses from: variant 0 / 1 run the SIMT
-// kernel at MINB = 2 / 3 CTAs per SM (more resident pairs per SM hide the
-// serial phases of each pair's factorisation; fewer leave more registers per
-// thread); variant 2 (mixed precision only) is the tensor-core kernel at 3.
-// Each variant lives in its own translation unit under csrc/inst/.
+// Forward variants the autotuner chooses from (kFwdLook, kFwdCtasPerSm):
+// variant 0 / 1 run the SIMT kernel at MINB = 2 / 3 CTAs per SM (more resident
+// pairs per SM hide the serial phases of each pair's factorisation; fewer
+// leave more registers per thread); variant 2 (mixed precision only) is the
+// tensor-core kernel at 3; variant 3 is variant 1 with Cholesky look-ahead
+// groups of 16 panels instead of 8.  Each variant lives in its own
+// translation unit under csrc/inst/.
 cudaError_t launch_forward(const FwdParams& prm, int precision, int variant, int n_ctas,
                            cudaStream_t s) {
   if (precision == 0) {
+    if (variant == 3) return launch_fwd_f64_3_l16(prm, n_ctas, s);
     if (variant == 1) return launch_fwd_f64_3(prm, n_ctas, s);
     return launch_fwd_f64_2(prm, n_ctas, s);
   }
+  if (variant == 3) return launch_fwd_f32_3_l16(prm, n_ctas, s);
   if (variant == 2) return launch_fwd_tc_3(prm, n_ctas, s);
   if (variant == 1) return launch_fwd_f32_3(prm, n_ctas, s);
   return launch_fwd_f32_2(prm, n_ctas, s);
@@ -31,10 +35,12 @@ cudaError_t launch_forward(const FwdParams& prm, int precision, int variant, int
 
 int forward_blocks_per_sm(int precision, int variant) {
   if (precision == 0) {
+    if (variant == 3) return occupancy_fwd_f64_3_l16();
     if (variant == 1) return occupancy_fwd_f64_3();
     if (variant == 0) return occupancy_fwd_f64_2();
     return 0;
   }
+  if (variant == 3) return occupancy_fwd_f32_3_l16();
   if (variant == 2) return occupancy_fwd_tc_3();
   if (variant == 1) return occupancy_fwd_f32_3();
   return occupancy_fwd_f32_2();

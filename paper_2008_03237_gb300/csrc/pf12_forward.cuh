@@ -28,7 +28,7 @@ __device__ __forceinline__ void write_pair_energy(const FwdParams& prm, int64_t 
   prm.status[P] = (isfinite(D) && isfinite(X)) ? 0 : 2;
 }
 
-template <typename TC>
+template <typename TC, int LOOK = kLook>
 __device__ bool pair_forward(const FwdParams& prm, const PairDesc& pd, double* ws, GemmSmem& gs,
                              CholSmem& cs, double (*red)[kThreads / 32], SieveCtl& sc,
                              uint32_t& phase) {
@@ -74,7 +74,7 @@ __device__ bool pair_forward(const FwdParams& prm, const PairDesc& pd, double* w
   if (pd.s) __syncthreads();
 
   // S2: FP64 Cholesky of J_g with the forward solve of [At^g_i; At^g_j]
-  const bool ok = chol_augmented(M, ld, m, m + 2 * k, cs, gs);
+  const bool ok = chol_augmented<LOOK>(M, ld, m, m + 2 * k, cs, gs);
   if (!ok) {
     if (tid == 0) {
       const double nan = __longlong_as_double(0x7ff8000000000000ll);
@@ -135,7 +135,7 @@ __device__ bool pair_forward(const FwdParams& prm, const PairDesc& pd, double* w
   return true;
 }
 
-template <typename TC, int MINB>
+template <typename TC, int MINB, int LOOK = kLook>
 __global__ void __launch_bounds__(kThreads, MINB) pair_forward_kernel(FwdParams prm) {
   __shared__ GemmSmem gs;
   __shared__ CholSmem cs;
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_forward_kernel(FwdParams 
     __syncthreads();
     if (slot < 0 || slot >= prm.n_pairs) break;
     const PairDesc pd = prm.desc[slot];
-    if (!pair_forward<TC>(prm, pd, ws, gs, cs, red, sc, phase)) {
+    if (!pair_forward<TC, LOOK>(prm, pd, ws, gs, cs, red, sc, phase)) {
       if (threadIdx.x == 0) {
         prm.status[pd.pair] = 3;
         atomicExch(prm.err, 1);

@@ -201,6 +201,10 @@ cudaError_t launch_fwd_f64_3(const FwdParams& prm, int n_ctas, cudaStream_t s);
 cudaError_t launch_fwd_f32_2(const FwdParams& prm, int n_ctas, cudaStream_t s);
 cudaError_t launch_fwd_f32_3(const FwdParams& prm, int n_ctas, cudaStream_t s);
 cudaError_t launch_fwd_tc_3(const FwdParams& prm, int n_ctas, cudaStream_t s);
+cudaError_t launch_fwd_f64_3_l16(const FwdParams& prm, int n_ctas, cudaStream_t s);
+cudaError_t launch_fwd_f32_3_l16(const FwdParams& prm, int n_ctas, cudaStream_t s);
+int occupancy_fwd_f64_3_l16();
+int occupancy_fwd_f32_3_l16();
 int occupancy_fwd_f64_2();
 int occupancy_fwd_f64_3();
 int occupancy_fwd_f32_2();
@@ -215,7 +219,13 @@ int occupancy_bwd_f64_3();
 int occupancy_bwd_f32_2();
 int occupancy_bwd_f32_3();
 
-constexpr int kFwdVariants = 3;
+// Forward variants (tile shapes) the autotuner chooses from:
+//   0: SIMT, 2 CTAs/SM, look-ahead 8    1: SIMT, 3 CTAs/SM, look-ahead 8
+//   2: tcgen05 contractions, 3 CTAs/SM, look-ahead 8 (mixed precision only)
+//   3: SIMT, 3 CTAs/SM, look-ahead 16
+constexpr int kFwdVariants = 4;
+constexpr int kFwdLook[kFwdVariants] = {8, 8, 8, 16};
+constexpr int kFwdCtasPerSm[kFwdVariants] = {2, 3, 3, 3};
 cudaError_t launch_forward(const FwdParams& prm, int precision, int variant, int n_ctas,
                            cudaStream_t s);
 constexpr int kBwdVariants = 2;
