@@ -51,13 +51,61 @@ def plan_batches(n_pao, n_pno, n_aux, budget_bytes):
     return out
 
 
+class ResumeRecord:
+    """Batch-level resume record of a streamed run: which batches are done,
+    their totals, pair energies and statuses.  Written atomically (temporary
+    file + rename) after every batch, so a run that stops (an exception in a
+    producer, a lost process) restarts at the first unfinished batch and
+    reproduces the uninterrupted result bit for bit."""
+
+    def __init__(self, path, batches, n_pairs):
+        self.path = path
+        self.batches = np.asarray(batches, np.int64).reshape(-1, 2)
+        self.n = int(n_pairs)
+        self.done = np.zeros(len(self.batches), bool)
+        self.totals = np.zeros(len(self.batches))
+        self.e_pair = np.zeros((self.n, 3))
+        self.status = np.zeros(self.n, np.int32)
+
+    @classmethod
+    def open(cls, path, batches, n_pairs):
+        """The record at path if it belongs to the same batch plan, else a new one."""
+        import os
+        rec = cls(path, batches, n_pairs)
+        if path and os.path.exists(path):
+            with np.load(path) as z:
+                if (int(z["n"]) == rec.n and z["batches"].shape == rec.batches.shape
+                        and np.array_equal(z["batches"], rec.batches)):
+                    rec.done = z["done"].astype(bool)
+                    rec.totals = z["totals"].copy()
+                    rec.e_pair = z["e_pair"].copy()
+                    rec.status = z["status"].copy()
+        return rec
+
+    def commit(self, q, total, e_pair, status):
+        import os
+        b, e = self.batches[q]
+        self.e_pair[b:e] = e_pair
+        self.status[b:e] = status
+        self.totals[q] = total
+        self.done[q] = True
+        if self.path:
+            tmp = self.path + ".tmp.npz"
+            np.savez(tmp, n=self.n, batches=self.batches, done=self.done, totals=self.totals,
+                     e_pair=self.e_pair, status=self.status)
+            os.replace(tmp, self.path)
+
+
 class StreamedPairF12:
     """Runs the pair-F12 path batch by batch.
 
     producer(begin, end, tensors, layout) must fill the packed device tensors
     (keys Agi, Agj, Afi, Afj, Jg, Jf, Q, T) for pairs [begin, end) in the given
     layout.  grad_consumer(begin, end, grads, layout), when given, receives the
-    batch's gradients (same packed layout) before the buffers are reused."""
+    batch's gradients (same packed layout) before the buffers are reused.
+    checkpoint (a file path), when given, keeps a ResumeRecord: batches it
+    lists as done are not produced or evaluated again (nor handed to the
+    gradient consumer, which received them in the earlier run)."""
 
     def __init__(self, precision="mixed_fp32", budget_bytes=48e9, tuner_cache=None):
         self.precision = precision
@@ -65,37 +113,75 @@ class StreamedPairF12:
         self.tuner_cache = tuner_cache
 
     def run(self, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, producer, backward=False,
-            grad_consumer=None, dE=1.0):
+            grad_consumer=None, dE=1.0, checkpoint=None):
+        """Evaluates every batch; returns (E, e_pair (device, n x 3), status).
+
+        Two sets of input buffers alternate: while batch q is evaluated on the
+        current stream, the producer fills batch q + 1 on a side stream (torch's
+        current stream while it runs; it must order its device work on that
+        stream, not synchronise the device).  Its host work (for the synthetic
+        generator, the PNO coefficients and amplitudes) overlaps the GPU's."""
         n = len(pi)
         batches = plan_batches(n_pao, n_pno, n_aux, self.budget)
+        rec = ResumeRecord.open(checkpoint, batches, n)
         lays = [packed_layout(n_pao[b:e], n_pno[b:e], n_aux[b:e]) for b, e in batches]
         cap = {key: max([L[key] for L in lays] + [2]) for key in ("len_pm", "len_mm", "len_pk", "len_kk")}
         dev = "cuda"
-        t = {x: torch.zeros(cap["len_pm"], dtype=torch.float64, device=dev) for x in ("Agi", "Agj", "Afi", "Afj")}
-        t.update({x: torch.zeros(cap["len_mm"], dtype=torch.float64, device=dev) for x in ("Jg", "Jf")})
-        t["Q"] = torch.zeros(cap["len_pk"], dtype=torch.float64, device=dev)
-        t["T"] = torch.zeros(cap["len_kk"], dtype=torch.float64, device=dev)
+        todo = [q for q in range(len(batches)) if not rec.done[q]]
+        n_sets = 2 if len(todo) > 1 else 1
+        sets = []
+        for _ in range(n_sets):
+            t = {x: torch.zeros(cap["len_pm"], dtype=torch.float64, device=dev) for x in ("Agi", "Agj", "Afi", "Afj")}
+            t.update({x: torch.zeros(cap["len_mm"], dtype=torch.float64, device=dev) for x in ("Jg", "Jf")})
+            t["Q"] = torch.zeros(cap["len_pk"], dtype=torch.float64, device=dev)
+            t["T"] = torch.zeros(cap["len_kk"], dtype=torch.float64, device=dev)
+            sets.append(t)
         g = None
         if backward:
-            g = {x: torch.zeros_like(t[x]) for x in ("Agi", "Agj", "Afi", "Afj", "Q", "T")}
+            g = {x: torch.zeros_like(sets[0][x]) for x in ("Agi", "Agj", "Afi", "Afj", "Q", "T")}
         e_pair = torch.empty((max(n, 1), 3), dtype=torch.float64, device=dev)
         eng = PairF12(self.precision, tuner_cache=self.tuner_cache)
-        totals, status = [], np.zeros(n, np.int32)
-        for (b, e), lay in zip(batches, lays):
-            producer(b, e, t, lay)
+        compute = torch.cuda.current_stream()
+        side = torch.cuda.Stream()
+        produced = {}
+
+        def produce(i):
+            q = todo[i]
+            b, e = batches[q]
+            # the buffer set's previous batch (i - 1 of the same parity is i - 2)
+            # is complete: the host synchronised on its results before this call
+            with torch.cuda.stream(side):
+                producer(b, e, sets[i % n_sets], lays[q])
+                ev = torch.cuda.Event()
+                ev.record(side)
+            produced[i] = ev
+
+        self.resumed = int(rec.done.sum())
+        if todo:
+            produce(0)
+        for i, q in enumerate(todo):
+            b, e = batches[q]
+            t, lay = sets[i % n_sets], lays[q]
+            compute.wait_event(produced.pop(i))
             eng.upload_pairs(n_orb, orb_kind, pi[b:e], pj[b:e], n_pao[b:e], n_pno[b:e], n_aux[b:e],
                              t, lay)
             eng.fit()
+            if i + 1 < len(todo) and n_sets == 2:
+                produce(i + 1)                     # overlaps this batch's evaluation
             Eb, _ = eng.energy(e_pair[b:e], check=False)
-            totals.append(Eb)
-            status[b:e] = eng.pair_status()
+            st_b = eng.pair_status()
             if backward:
                 eng.backward(dE, g)
                 if grad_consumer is not None:
                     grad_consumer(b, e, g, lay)
+            rec.commit(q, Eb, e_pair[b:e].cpu().numpy(), st_b)
+            if i + 1 < len(todo) and n_sets == 1:
+                produce(i + 1)
         torch.cuda.synchronize()
+        e_pair[:n].copy_(torch.from_numpy(rec.e_pair))
+        status = rec.status.copy()
         E = 0.0
-        for x in totals:
+        for x in rec.totals:
             E += x
         self.stats = eng.stats()
         eng.close()

@@ -123,7 +123,7 @@ def fill(wl, t, lay, scratch_bytes=1 << 30):
         tt[o:o + T.size] = T.ravel()
     t["Q"][:q.size].copy_(torch.from_numpy(q))
     t["T"][:tt.size].copy_(torch.from_numpy(tt))
-    torch.cuda.synchronize()
+    torch.cuda.current_stream().synchronize()   # this stream only: callers may overlap it
     return t
 
 

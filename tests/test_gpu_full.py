@@ -162,3 +162,49 @@ def test_full_graph_replay_is_deterministic(built):
         E2, e2 = eng.energy()
         assert E2 == E1 and np.array_equal(e2.cpu().numpy(), e1)
     assert eng.stats()["graph_used"] == 1
+
+
+def test_full_c40h81_list_sampled_against_the_oracle(built):
+    """The complete pair energy at the size bench.py times (the whole C40H81
+    chain, device-drawn inputs, one persistent launch, mixed and FP64): sampled
+    pairs one by one against the oracle (the largest and smallest domains,
+    diagonal, SOMO and random pairs), properties over every pair, and the
+    mixed total against FP64 on the chemical scale."""
+    import paper_2008_03237_gb300 as pf
+    from synthetic import device
+    wl = S.c40h81()
+    t, lay = device.allocate_full(wl)
+    device.fill_full(wl, t, lay)
+    out = {}
+    for prec in ("fp64", "mixed_fp32"):
+        eng = pf.PairF12(prec)
+        eng.upload_full(wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux, t, lay)
+        eng.fit()
+        E, e = eng.energy()
+        out[prec] = (E, e.cpu().numpy(), eng.full_terms().cpu().numpy(), eng.pair_status())
+        eng.close()
+    del t
+    E64, e64, tm64, st64 = out["fp64"]
+    Emx, emx, _, stmx = out["mixed_fp32"]
+    assert (st64 == 0).all() and (stmx == 0).all()
+    assert np.isfinite(e64).all() and np.isfinite(emx).all()
+    diag = wl.pi == wl.pj
+    assert (e64[diag, 1:] == 0.0).all()
+    somo = wl.orb_kind == 1
+    ss = somo[wl.pi] & somo[wl.pj]
+    assert (e64[ss, 0] == 0.0).all() and (e64[ss, 2] == 0.0).all()
+    sd = somo[wl.pi] ^ somo[wl.pj]
+    assert (e64[sd, 2] == 0.0).all()
+    picks = {int(np.argmax(wl.n_aux)), int(np.argmin(wl.n_aux)), int(np.argmax(wl.n_pao)),
+             int(np.argmax(wl.n_pno)), int(np.nonzero(diag)[0][7])}
+    picks.update(int(x) for x in np.nonzero(somo[wl.pi] | somo[wl.pj])[0][:2])
+    picks.update(int(x) for x in np.random.default_rng(5).choice(wl.n_pairs, 5, replace=False))
+    picks = sorted(picks)
+    ref = F.run(wl, pairs=picks)
+    for q, P in enumerate(picks):
+        assert np.abs(e64[P] - ref["e_pair"][q]).max() <= 1e-10, P
+        scale = np.abs(ref["terms"][q]).max()
+        assert np.abs(tm64[P] - ref["terms"][q]).max() <= 1e-11 * scale, P
+        assert np.abs(emx[P] - ref["e_pair"][q]).max() <= 1e-5 * np.abs(ref["e_pair"][q]).max(), P
+    sum_abs = float(np.abs(e64.sum(axis=1)).sum())
+    assert normalised_error(Emx - E64, sum_abs, wl.n_orb) <= 1e-6

@@ -100,3 +100,39 @@ def test_host_pipelined_equals_resident(built, tmp_path):
     assert nb >= 3 and (st == 0).all()
     assert np.array_equal(e.cpu().numpy(), one["e_pair"])
     assert abs(E - one["E"]) <= 1e-12 * np.abs(one["e_pair"]).sum()
+
+
+def test_streamed_run_resumes_after_a_failed_batch(built, tmp_path):
+    """Failure injected on the host: the producer of the third batch raises.
+    The resume record keeps the finished batches; a second run with the same
+    record produces and evaluates only the rest and returns the uninterrupted
+    result bit for bit."""
+    from paper_2008_03237_gb300.stream import StreamedPairF12, input_bytes
+    wl = S.custom(6, 2, 4, (30, 90), ("uniform", 3, 40), (40, 160), name="stream-resume")
+    budget = input_bytes(wl.n_pao, wl.n_pno, wl.n_aux).sum() / 4.5
+    args = (wl.n_orb, wl.orb_kind, wl.pi, wl.pj, wl.n_pao, wl.n_pno, wl.n_aux)
+    ref = StreamedPairF12("fp64", budget_bytes=budget)
+    E_ref, e_ref, _ = ref.run(*args, _producer(wl))
+    e_ref = e_ref.cpu().numpy().copy()
+    ck = str(tmp_path / "resume.npz")
+    good = _producer(wl)
+    calls = []
+
+    def failing(b, e, t, lay):
+        if len(calls) == 2:
+            raise RuntimeError("injected producer failure")
+        calls.append((b, e))
+        good(b, e, t, lay)
+    sp = StreamedPairF12("fp64", budget_bytes=budget)
+    with pytest.raises(RuntimeError, match="injected"):
+        sp.run(*args, failing, checkpoint=ck)
+    again = []
+
+    def counting(b, e, t, lay):
+        again.append((b, e))
+        good(b, e, t, lay)
+    sp2 = StreamedPairF12("fp64", budget_bytes=budget)
+    E, e, st = sp2.run(*args, counting, checkpoint=ck)
+    assert sp2.resumed == 2 and len(again) == len(sp2.batches) - 2
+    assert (st == 0).all()
+    assert np.array_equal(e.cpu().numpy(), e_ref) and E == E_ref

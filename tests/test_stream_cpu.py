@@ -65,3 +65,24 @@ def test_packed_metric_layout():
     assert lay_t["len_mm"] == int(((m * (m + 1) // 2 + 31) // 32 * 32).sum())
     for key in ("off_pm", "off_pk", "off_kk"):
         assert np.array_equal(lay_t[key], lay_f[key])
+
+
+def test_resume_record_round_trip_and_plan_check(tmp_path):
+    """The batch-level resume record (the checkpoint of a streamed run): what a
+    run commits is what the next run reads back, and a record of another batch
+    plan is ignored."""
+    from paper_2008_03237_gb300.stream import ResumeRecord
+    path = str(tmp_path / "rec.npz")
+    batches = [(0, 3), (3, 7), (7, 10)]
+    rec = ResumeRecord.open(path, batches, 10)
+    assert not rec.done.any()
+    rng = np.random.default_rng(1)
+    e1 = rng.standard_normal((4, 3))
+    rec.commit(1, 2.5, e1, np.array([0, 0, 1, 0], np.int32))
+    back = ResumeRecord.open(path, batches, 10)
+    assert list(back.done) == [False, True, False]
+    assert back.totals[1] == 2.5 and np.array_equal(back.e_pair[3:7], e1)
+    assert list(back.status[3:7]) == [0, 0, 1, 0]
+    other = ResumeRecord.open(path, [(0, 5), (5, 10)], 10)     # another plan: start afresh
+    assert not other.done.any()
+    assert not ResumeRecord.open(path, batches, 11).done.any()
