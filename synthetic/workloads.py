@@ -23,7 +23,9 @@ value is an exact integer times one FP64 constant and host and device produce
 identical bits.  Q alone is orthonormalised on the host (numpy QR) and uploaded.
 """
 from dataclasses import dataclass, field
+import json
 import math
+import os
 
 import numpy as np
 
@@ -214,28 +216,49 @@ def make_lattice(name, n_domo, n_somo, side, r_cut, pao, pno, aux, seed):
     return Workload(name, seed, n_domo, n_somo, kind, pi, pj, p, k, m, decay)
 
 
+CONFIG_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "configs")
+
+
+def from_config(name_or_path):
+    """Workload described by a JSON file of configs/ (by name) or at a path:
+    kind "chain" (n_domo, n_somo, cutoff) or "lattice" (n_domo, n_somo, side,
+    r_cut), size ranges pao, pno, aux, and seed SEED_BASE + seed_offset."""
+    path = name_or_path
+    if os.path.sep not in path and not path.endswith(".json"):
+        path = os.path.join(CONFIG_DIR, path + ".json")
+    with open(path) as fh:
+        c = json.load(fh)
+    pno = tuple(c["pno"])
+    seed = SEED_BASE + int(c["seed_offset"])
+    if c["kind"] == "chain":
+        return make_chain(c["label"], c["n_domo"], c["n_somo"], c["cutoff"], tuple(c["pao"]), pno,
+                          tuple(c["aux"]), seed)
+    if c["kind"] == "lattice":
+        return make_lattice(c["label"], c["n_domo"], c["n_somo"], c["side"], c["r_cut"],
+                            tuple(c["pao"]), pno, tuple(c["aux"]), seed)
+    raise ValueError(f"unknown workload kind {c['kind']!r} in {path}")
+
+
 def tiny():
-    """7 DOMO + 1 SOMO, all 36 pairs, p = 30, k ~ U[8,16], m ~ U[60,120]."""
-    return make_chain("tiny-doublet-8orb", 7, 1, None, (30, 30), ("uniform", 8, 16),
-                      (60, 120), SEED_BASE + 0)
+    """7 DOMO + 1 SOMO, all 36 pairs, p = 30, k ~ U[8,16], m ~ U[60,120] (configs/tiny.json)."""
+    return from_config("tiny")
 
 
 def c40h81():
-    """C40H81-radical chain: 120 DOMO + 1 SOMO, |i-j| <= 25 (2,821 unique pairs)."""
-    return make_chain("C40H81-chain", 120, 1, 25, (80, 200), ("lognormal", 25, 0.4, 8, 60),
-                      (300, 800), SEED_BASE + 1)
+    """C40H81-radical chain: 120 DOMO + 1 SOMO, |i-j| <= 25 (2,821 unique pairs; configs/c40h81.json)."""
+    return from_config("c40h81")
 
 
 def c160h321():
-    """C160H321-radical chain: 480 DOMO + 1 SOMO, |i-j| <= 30 (14,446 unique pairs)."""
-    return make_chain("C160H321-chain", 480, 1, 30, (100, 250), ("lognormal", 30, 0.45, 10, 70),
-                      (400, 1000), SEED_BASE + 2)
+    """C160H321-radical chain: 480 DOMO + 1 SOMO, |i-j| <= 30 (14,446 unique pairs;
+    configs/c160h321.json)."""
+    return from_config("c160h321")
 
 
 def lattice_quartet():
-    """700 DOMO + 3 SOMO on a 9x9x9 lattice, distance cutoff 3.0 (29,226 unique pairs)."""
-    return make_lattice("lattice-703-quartet", 700, 3, 9, 3.0, (150, 400),
-                        ("lognormal", 35, 0.45, 10, 80), (600, 1500), SEED_BASE + 4)
+    """700 DOMO + 3 SOMO on a 9x9x9 lattice, distance cutoff 3.0 (29,226 unique pairs;
+    configs/lattice703.json)."""
+    return from_config("lattice703")
 
 
 def custom(n_domo, n_somo, cutoff, pao, pno, aux, seed=SEED_BASE + 100, name="custom"):
