@@ -626,7 +626,7 @@ def main():
         return run_streamed(args, rank, world, local_rank)
     if args.shard and world > 1:
         return run_sharded(args, rank, world, local_rank)
-    if args.full:
+    if args.full and not args.stream_gb:
         return run_full(args, rank, world, local_rank)
     wl, f64, fmix, byts, o = run_ours(args, rank, world, local_rank)
     ms = o["ms"]
@@ -907,12 +907,14 @@ def run_streamed(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     __graft_entry__.build()
     wl = make_workload(args.workload, args.max_pairs, rank)
-    f64, fmix, byts = flops_bytes(wl)
+    f64, fmix, byts = full_flops(wl) if args.full else flops_bytes(wl)
+    fill = device.fill_full if args.full else device.fill
 
     def produce(b, e, t, lay):
-        device.fill(wl.subset(np.arange(b, e)), t, lay)
+        fill(wl.subset(np.arange(b, e)), t, lay)
     cache = os.path.join(tempfile.gettempdir(), f"pf12_tune_{os.getpid()}.txt")
-    sp = StreamedPairF12(args.precision, budget_bytes=args.stream_gb * 1e9, tuner_cache=cache)
+    sp = StreamedPairF12(args.precision, budget_bytes=args.stream_gb * 1e9, tuner_cache=cache,
+                         full=args.full)
     peak = [0]
     total_mem = torch.cuda.mem_get_info()[1]
 
@@ -941,10 +943,14 @@ def run_streamed(args, rank, world, local_rank):
             "dtype": "f64+f32" if args.precision != "fp64" else "f64",
             "data": "synthetic, drawn on the device batch by batch inside every step",
             "config": {"workload": wl.name, "pairs": wl.n_pairs, "precision": args.precision,
+                       "energy": ("complete E_(2)F12 per pair" if args.full
+                                  else "amplitude term (1/2 V t of Eq. Vtilde)"),
                        "streamed": True, "batch_budget_gb": args.stream_gb,
                        "batches": len(sp.batches), "backward": bool(args.backward),
                        "inputs_gb": byts / 1e9, "peak_device_gb": peak[0] / 1e9},
-            "tflops": {"fp64_forward": f64 / ms / 1e9},
+            "tflops": {"fp64_forward": f64 / ms / 1e9,
+                       "frac_of_fp64_peak": f64 / ms / 1e9 / FP64_PEAK_TFLOPS},
+            "overlap": "the next batch is drawn on a side stream while the current one is evaluated",
             "E_total_raw": E, "pairs_failed": int((st != 0).sum()),
             "clocks": sampler.summary(), "e2e": None}
     print(json.dumps(line), flush=True)

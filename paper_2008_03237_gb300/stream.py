@@ -30,14 +30,45 @@ def packed_layout(n_pao, n_pno, n_aux, align=ALIGN):
     return out
 
 
+def full_packed_layout(n_pao, n_pno, n_aux, align=ALIGN):
+    """Element offsets of the complete-pair-energy layout (see pf12_full_tensors):
+    off_pm ((p + 2) x m), off_mm, off_pk, off_kk, off_pp (p x p), off_s (2 x k),
+    off_b (k x m x (k + 2))."""
+    p, k, m = (np.asarray(a, np.int64) for a in (n_pao, n_pno, n_aux))
+    out = {}
+    for name, sz in (("pm", (p + 2) * m), ("mm", m * m), ("pk", p * k), ("kk", k * k),
+                     ("pp", p * p), ("s", 2 * k), ("b", k * m * (k + 2))):
+        padded = (sz + align - 1) // align * align
+        off = np.zeros(len(sz), np.int64)
+        if len(sz) > 1:
+            off[1:] = np.cumsum(padded)[:-1]
+        out["off_" + name] = off
+        out["len_" + name] = int(padded.sum()) if len(sz) else 0
+    return out
+
+
 def input_bytes(n_pao, n_pno, n_aux):
     p, k, m = (np.asarray(a, np.float64) for a in (n_pao, n_pno, n_aux))
     return 8.0 * (4 * p * m + 2 * m * m + p * k + k * k)
 
 
-def plan_batches(n_pao, n_pno, n_aux, budget_bytes):
-    """Contiguous [begin, end) ranges of pairs with inputs <= budget_bytes each."""
-    per = input_bytes(n_pao, n_pno, n_aux)
+def full_input_bytes(n_pao, n_pno, n_aux):
+    p, k, m = (np.asarray(a, np.float64) for a in (n_pao, n_pno, n_aux))
+    return 8.0 * (10 * (p + 2) * m + 3 * m * m + p * k + k * k + p * p + 2 * k + k * m * (k + 2))
+
+
+# full-mode tensors and the layout key of each
+FULL_KEYS = {**{n: "pm" for n in ("Agi", "Agj", "Afi", "Afj", "Ari", "Arj", "AgiF", "AgjF", "AriF",
+                                  "ArjF")},
+             "Jg": "mm", "Jf": "mm", "Jr": "mm", "Q": "pk", "T": "kk", "Fv": "pp", "S": "s", "B": "b"}
+PLAIN_KEYS = {"Agi": "pm", "Agj": "pm", "Afi": "pm", "Afj": "pm", "Jg": "mm", "Jf": "mm",
+              "Q": "pk", "T": "kk"}
+
+
+def plan_batches(n_pao, n_pno, n_aux, budget_bytes, per=None):
+    """Contiguous [begin, end) ranges of pairs with inputs <= budget_bytes each
+    (per: bytes of each pair, default the amplitude-term inputs)."""
+    per = input_bytes(n_pao, n_pno, n_aux) if per is None else np.asarray(per, np.float64)
     if len(per) and per.max() > budget_bytes:
         raise ValueError("one pair alone exceeds the batch budget")
     out, beg, acc = [], 0, 0.0
@@ -107,10 +138,13 @@ class StreamedPairF12:
     lists as done are not produced or evaluated again (nor handed to the
     gradient consumer, which received them in the earlier run)."""
 
-    def __init__(self, precision="mixed_fp32", budget_bytes=48e9, tuner_cache=None):
+    def __init__(self, precision="mixed_fp32", budget_bytes=48e9, tuner_cache=None, full=False):
+        """full: the complete pair energy (pf12_upload_full; tensors FULL_KEYS,
+        layout full_packed_layout); no adjoint in that mode."""
         self.precision = precision
         self.budget = float(budget_bytes)
         self.tuner_cache = tuner_cache
+        self.full = bool(full)
 
     def run(self, n_orb, orb_kind, pi, pj, n_pao, n_pno, n_aux, producer, backward=False,
             grad_consumer=None, dE=1.0, checkpoint=None):
@@ -122,20 +156,20 @@ class StreamedPairF12:
         stream, not synchronise the device).  Its host work (for the synthetic
         generator, the PNO coefficients and amplitudes) overlaps the GPU's."""
         n = len(pi)
-        batches = plan_batches(n_pao, n_pno, n_aux, self.budget)
+        if self.full and backward:
+            raise ValueError("the complete pair energy has no adjoint")
+        keys = FULL_KEYS if self.full else PLAIN_KEYS
+        layout = full_packed_layout if self.full else packed_layout
+        per = (full_input_bytes if self.full else input_bytes)(n_pao, n_pno, n_aux)
+        batches = plan_batches(n_pao, n_pno, n_aux, self.budget, per)
         rec = ResumeRecord.open(checkpoint, batches, n)
-        lays = [packed_layout(n_pao[b:e], n_pno[b:e], n_aux[b:e]) for b, e in batches]
-        cap = {key: max([L[key] for L in lays] + [2]) for key in ("len_pm", "len_mm", "len_pk", "len_kk")}
+        lays = [layout(n_pao[b:e], n_pno[b:e], n_aux[b:e]) for b, e in batches]
+        cap = {key: max([L["len_" + key] for L in lays] + [2]) for key in set(keys.values())}
         dev = "cuda"
         todo = [q for q in range(len(batches)) if not rec.done[q]]
         n_sets = 2 if len(todo) > 1 else 1
-        sets = []
-        for _ in range(n_sets):
-            t = {x: torch.zeros(cap["len_pm"], dtype=torch.float64, device=dev) for x in ("Agi", "Agj", "Afi", "Afj")}
-            t.update({x: torch.zeros(cap["len_mm"], dtype=torch.float64, device=dev) for x in ("Jg", "Jf")})
-            t["Q"] = torch.zeros(cap["len_pk"], dtype=torch.float64, device=dev)
-            t["T"] = torch.zeros(cap["len_kk"], dtype=torch.float64, device=dev)
-            sets.append(t)
+        sets = [{x: torch.zeros(cap[key], dtype=torch.float64, device=dev) for x, key in keys.items()}
+                for _ in range(n_sets)]
         g = None
         if backward:
             g = {x: torch.zeros_like(sets[0][x]) for x in ("Agi", "Agj", "Afi", "Afj", "Q", "T")}
@@ -163,11 +197,15 @@ class StreamedPairF12:
             b, e = batches[q]
             t, lay = sets[i % n_sets], lays[q]
             compute.wait_event(produced.pop(i))
-            eng.upload_pairs(n_orb, orb_kind, pi[b:e], pj[b:e], n_pao[b:e], n_pno[b:e], n_aux[b:e],
-                             t, lay)
+            upload = eng.upload_full if self.full else eng.upload_pairs
+            upload(n_orb, orb_kind, pi[b:e], pj[b:e], n_pao[b:e], n_pno[b:e], n_aux[b:e], t, lay)
             eng.fit()
+            failure = None
             if i + 1 < len(todo) and n_sets == 2:
-                produce(i + 1)                     # overlaps this batch's evaluation
+                try:
+                    produce(i + 1)                 # overlaps this batch's evaluation
+                except Exception as exc:           # finish and record this batch first
+                    failure = exc
             Eb, _ = eng.energy(e_pair[b:e], check=False)
             st_b = eng.pair_status()
             if backward:
@@ -175,6 +213,9 @@ class StreamedPairF12:
                 if grad_consumer is not None:
                     grad_consumer(b, e, g, lay)
             rec.commit(q, Eb, e_pair[b:e].cpu().numpy(), st_b)
+            if failure is not None:
+                eng.close()
+                raise failure
             if i + 1 < len(todo) and n_sets == 1:
                 produce(i + 1)
         torch.cuda.synchronize()

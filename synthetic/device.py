@@ -3,7 +3,7 @@ host generator in workloads.py), for workloads too large to draw on the host.
 
 Uses libpf12synth.so (synthetic/csrc/synth_gen.cu): Philox4x32-10 draws of the
 DF factors and of the integer matrices behind J = c2 Z Z^T + 0.1 I.  Q and T
-are drawn on the host and copied.
+are drawn on the host first and copied last.
 """
 import ctypes
 import os
@@ -73,6 +73,7 @@ def fill(wl, t, lay, scratch_bytes=1 << 30):
     n = wl.n_pairs
     if n == 0:
         return t
+    q, tt = host_pno_and_amplitudes(wl, lay)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     keys = np.array([wl.pair_key(P) for P in range(n)], np.int32)
     diag = wl.pi == wl.pj
@@ -112,19 +113,26 @@ def fill(wl, t, lay, scratch_bytes=1 << 30):
             if rc != 0:
                 raise RuntimeError(f"synth_fill_metrics failed ({rc})")
         del scratch
+    t["Q"][:q.size].copy_(torch.from_numpy(q))
+    t["T"][:tt.size].copy_(torch.from_numpy(tt))
+    torch.cuda.current_stream().synchronize()   # this stream only: callers may overlap it
+    return t
+
+
+def host_pno_and_amplitudes(wl, lay):
+    """Q and T of every pair of wl, drawn on the host into packed arrays.  The
+    fills draw these first: this host work then overlaps whatever the device
+    is still running, before the device fills queue behind it."""
     q = np.zeros(lay["len_pk"])
     tt = np.zeros(lay["len_kk"])
-    for P in range(n):
+    for P in range(wl.n_pairs):
         Q = W.pno_coefficients(wl, P)
         T = W.amplitudes(wl, P)
         o = lay["off_pk"][P]
         q[o:o + Q.size] = Q.ravel()
         o = lay["off_kk"][P]
         tt[o:o + T.size] = T.ravel()
-    t["Q"][:q.size].copy_(torch.from_numpy(q))
-    t["T"][:tt.size].copy_(torch.from_numpy(tt))
-    torch.cuda.current_stream().synchronize()   # this stream only: callers may overlap it
-    return t
+    return q, tt
 
 
 FULL_META = np.dtype([("dst", "<i8"), ("src", "<i8"), ("p", "<i4"), ("k", "<i4"), ("m", "<i4"),
@@ -161,6 +169,7 @@ def fill_full(wl, t, lay, scratch_bytes=1 << 30):
     n = wl.n_pairs
     if n == 0:
         return t
+    q, tt = host_pno_and_amplitudes(wl, lay)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     seed = W_seed(wl)
     keys = np.array([wl.pair_key(P) for P in range(n)], np.int32)
@@ -246,18 +255,9 @@ def fill_full(wl, t, lay, scratch_bytes=1 << 30):
     gauss("S", lay["off_s"], 1, k, tid(FU.TID_S_I), cs)
     gauss("S", lay["off_s"] + k, 1, k, tid(FU.TID_S_J, FU.TID_S_I), cs)
     # Q, T from the host
-    q = np.zeros(lay["len_pk"])
-    tt = np.zeros(lay["len_kk"])
-    for P in range(n):
-        Q = W.pno_coefficients(wl, P)
-        T = W.amplitudes(wl, P)
-        o = lay["off_pk"][P]
-        q[o:o + Q.size] = Q.ravel()
-        o = lay["off_kk"][P]
-        tt[o:o + T.size] = T.ravel()
     t["Q"][:q.size].copy_(torch.from_numpy(q))
     t["T"][:tt.size].copy_(torch.from_numpy(tt))
-    torch.cuda.synchronize()
+    torch.cuda.current_stream().synchronize()   # this stream only: callers may overlap it
     return t
 
 

@@ -86,3 +86,18 @@ def test_resume_record_round_trip_and_plan_check(tmp_path):
     other = ResumeRecord.open(path, [(0, 5), (5, 10)], 10)     # another plan: start afresh
     assert not other.done.any()
     assert not ResumeRecord.open(path, batches, 11).done.any()
+
+
+def test_full_layout_matches_the_generator_layout():
+    """The executor's complete-pair-energy layout is the generator's (and the
+    C ABI's pf12_full_tensors layout)."""
+    from paper_2008_03237_gb300.stream import full_input_bytes, full_packed_layout
+    from synthetic.full import full_offsets
+    wl = S.custom(6, 1, 3, (10, 50), ("uniform", 2, 9), (5, 70))
+    a = full_packed_layout(wl.n_pao, wl.n_pno, wl.n_aux)
+    b = full_offsets(wl)
+    for key in b:
+        assert np.array_equal(np.asarray(a[key]), np.asarray(b[key])), key
+    p, k, m = (wl.n_pao.astype(float), wl.n_pno.astype(float), wl.n_aux.astype(float))
+    lens = 8.0 * (10 * (p + 2) * m + 3 * m * m + p * k + k * k + p * p + 2 * k + k * m * (k + 2))
+    assert np.allclose(full_input_bytes(wl.n_pao, wl.n_pno, wl.n_aux), lens)
