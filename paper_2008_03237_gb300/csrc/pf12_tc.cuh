@@ -8,13 +8,17 @@
 // with A(r, t) = TA ? A[t * lda + r] : A[r * lda + t] (FP64 in global memory)
 // and  B(n, t) = TB ? B[t * ldb + n] : B[n * ldb + t];
 // K is consumed in 32-wide chunks staged by all threads (FP64 -> FP32 -> tf32
-// hi/lo, canonical K-major layout without swizzle), one thread issues the
+// hi/lo, canonical K-major layout without swizzle; the FP64 <-> FP32
+// conversions run on the integer pipes, not on the FP64 pipe that bounds the
+// pair kernels), one thread issues the
 // MMAs, a commit to an mbarrier signals completion, and after every chunk the
 // FP32 accumulator is added into the FP64 output Out[n * ldo + r] (scaled by
 // alpha): short FP32 spans keep the accumulator's rounding bias small.  Every wait is bounded; on expiry the routine returns false.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "pf12_device.cuh"   // FP64 <-> FP32 conversions on the integer pipes
 
 namespace pf12 {
 namespace tc {
@@ -166,7 +170,7 @@ __device__ bool gemm_tile(int M, int N, int K, const double* A, int64_t lda, con
       else    { t = e % kKC; r = e / kKC; } // coalesced along t
       float x = 0.f;
       if (r < rows && k0 + t < K)
-        x = (float)(TA ? A[(int64_t)(k0 + t) * lda + r0 + r] : A[(int64_t)(r0 + r) * lda + k0 + t]);
+        x = f64_to_f32_rne(TA ? A[(int64_t)(k0 + t) * lda + r0 + r] : A[(int64_t)(r0 + r) * lda + k0 + t]);
       const uint32_t hi = to_tf32(x);
       const uint32_t lo = to_tf32(x - __uint_as_float(hi));
       const uint32_t off = kmajor_offset(r, t) >> 2;
@@ -180,7 +184,7 @@ __device__ bool gemm_tile(int M, int N, int K, const double* A, int64_t lda, con
       else    { t = e % kKC; n = e / kKC; }
       float x = 0.f;
       if (n < ncols && k0 + t < K)
-        x = (float)(TB ? B[(int64_t)(k0 + t) * ldb + n0 + n] : B[(int64_t)(n0 + n) * ldb + k0 + t]);
+        x = f64_to_f32_rne(TB ? B[(int64_t)(k0 + t) * ldb + n0 + n] : B[(int64_t)(n0 + n) * ldb + k0 + t]);
       const uint32_t hi = to_tf32(x);
       const uint32_t lo = to_tf32(x - __uint_as_float(hi));
       const uint32_t off = kmajor_offset(n, t) >> 2;
@@ -241,7 +245,7 @@ __device__ bool gemm_tile(int M, int N, int K, const double* A, int64_t lda, con
             const int n = cb + j;
             if (n < ncols) {
               double* po = Out + (int64_t)(n0 + n) * ldo + r0 + r;
-              const double val = alpha * (double)__uint_as_float(v[j]);
+              const double val = alpha * f32_to_f64(__uint_as_float(v[j]));
               *po = (accumulate || ch >= kPromote) ? *po + val : val;
             }
           }

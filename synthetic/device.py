@@ -73,7 +73,7 @@ def fill(wl, t, lay, scratch_bytes=1 << 30):
     n = wl.n_pairs
     if n == 0:
         return t
-    q, tt = host_pno_and_amplitudes(wl, lay)
+    q_host, t_host = host_pno_and_amplitudes(wl, lay)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     keys = np.array([wl.pair_key(P) for P in range(n)], np.int32)
     diag = wl.pi == wl.pj
@@ -113,8 +113,8 @@ def fill(wl, t, lay, scratch_bytes=1 << 30):
             if rc != 0:
                 raise RuntimeError(f"synth_fill_metrics failed ({rc})")
         del scratch
-    t["Q"][:q.size].copy_(torch.from_numpy(q))
-    t["T"][:tt.size].copy_(torch.from_numpy(tt))
+    t["Q"][:q_host.size].copy_(torch.from_numpy(q_host))
+    t["T"][:t_host.size].copy_(torch.from_numpy(t_host))
     torch.cuda.current_stream().synchronize()   # this stream only: callers may overlap it
     return t
 
@@ -169,7 +169,7 @@ def fill_full(wl, t, lay, scratch_bytes=1 << 30):
     n = wl.n_pairs
     if n == 0:
         return t
-    q, tt = host_pno_and_amplitudes(wl, lay)
+    q_host, t_host = host_pno_and_amplitudes(wl, lay)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     seed = W_seed(wl)
     keys = np.array([wl.pair_key(P) for P in range(n)], np.int32)
@@ -255,8 +255,8 @@ def fill_full(wl, t, lay, scratch_bytes=1 << 30):
     gauss("S", lay["off_s"], 1, k, tid(FU.TID_S_I), cs)
     gauss("S", lay["off_s"] + k, 1, k, tid(FU.TID_S_J, FU.TID_S_I), cs)
     # Q, T from the host
-    t["Q"][:q.size].copy_(torch.from_numpy(q))
-    t["T"][:tt.size].copy_(torch.from_numpy(tt))
+    t["Q"][:q_host.size].copy_(torch.from_numpy(q_host))
+    t["T"][:t_host.size].copy_(torch.from_numpy(t_host))
     torch.cuda.current_stream().synchronize()   # this stream only: callers may overlap it
     return t
 
