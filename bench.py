@@ -116,19 +116,25 @@ def make_workload(name, max_pairs, rank=0):
     return wl
 
 
-# DRAM bytes (read + write) of one launch of the SIMT 3-CTAs/SM forward kernel,
-# measured by ncu on a 1,368-pair subset of the C160H321 chain (16.9 GB of
-# algorithmic input bytes); scaled to other lists by algorithmic input bytes.
-TRAFFIC_CAPTURE = {"bytes": 85.735969e9, "alg_bytes": 16898189704.0, "variant": 1,
-                   "precision": "mixed_fp32"}
+# DRAM bytes (read + write) of one launch of a forward kernel variant, measured
+# by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on a deterministic
+# subset of the C160H321 chain; scaled to other lists by algorithmic input
+# bytes.  Variant 1 (SIMT, 3 CTAs/SM, look-ahead 8): 1,368 pairs, 16.9 GB of
+# algorithmic input bytes.  Variant 3 (SIMT, 3 CTAs/SM, look-ahead 16): 400
+# pairs, 5.01 GB.
+TRAFFIC_CAPTURE = {
+    1: {"bytes": 85.735969e9, "alg_bytes": 16898189704.0, "precision": "mixed_fp32"},
+    3: {"bytes": 17845812736.0 + 4430136576.0, "alg_bytes": 5011263536.0,
+        "precision": "mixed_fp32"},
+}
 
 
 def traffic_bytes(args, wl, byts, variant):
     """Per-launch DRAM traffic of the dominant kernel, from the ncu capture of
     the same kernel variant scaled by algorithmic bytes; None when the timed
-    kernel is not the captured one."""
-    cap = TRAFFIC_CAPTURE
-    if (variant != cap["variant"] or args.precision != cap["precision"] or args.stream_gb
+    kernel is not a captured one."""
+    cap = TRAFFIC_CAPTURE.get(variant)
+    if (cap is None or args.precision != cap["precision"] or args.stream_gb
             or args.augment_somo):
         return None
     return cap["bytes"] * byts / cap["alg_bytes"]
@@ -423,7 +429,7 @@ def run_ours(args, rank, world, local_rank):
     # plain FP64 mode of the same step, and the error of the headline energies against it
     if not args.no_fp64_compare and args.precision != "fp64":
         eng = make("fp64")
-        ms64 = timed(eng, max(2, args.steps // 2), 1)
+        ms64 = timed(eng, min(4, max(2, args.steps // 2)), 1)
         E64, e64 = eng.energy()
         e64 = e64.cpu().numpy()
         eng.close()
@@ -592,7 +598,7 @@ def run_e2e(args, wl_full, t_full, lay_full, pf, torch):
         step()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    steps = max(2, args.steps)
+    steps = min(5, max(2, args.steps))
     for _ in range(steps):
         E_e2e, nb = step()
     torch.cuda.synchronize()
@@ -601,7 +607,7 @@ def run_e2e(args, wl_full, t_full, lay_full, pf, torch):
     del host, streamer
     torch.cuda.empty_cache()
     return {"value": n / dt, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": 32 + 4 * n, "pairs": n, "ms_per_step": dt * 1e3,
+            "d2h_bytes_per_step": 32 + 4 * n, "pairs": n, "ms_per_step": dt * 1e3, "steps": steps,
             "host_budget_gb": budget / 1e9,
             "workload": wl.name, "arrival_groups": nb, "h2d_gbs_raw": h2d_gbs,
             "metric_layout": "packed lower triangles",
