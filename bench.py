@@ -116,15 +116,14 @@ def make_workload(name, max_pairs, rank=0):
     return wl
 
 
-# DRAM bytes (read + write) of one launch of a forward kernel variant, measured
-# by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on a deterministic
-# subset of the C160H321 chain; scaled to other lists by algorithmic input
-# bytes.  Variant 1 (SIMT, 3 CTAs/SM, look-ahead 8): 1,368 pairs, 16.9 GB of
-# algorithmic input bytes.  Variant 3 (SIMT, 3 CTAs/SM, look-ahead 16): 400
-# pairs, 5.01 GB.
+# DRAM bytes (read + write) of one launch of the forward kernel, measured by
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum) on a deterministic subset
+# of the C160H321 chain and scaled to other lists by algorithmic input bytes.
+# Only the variant whose current code was captured is listed: variant 3 (SIMT,
+# 3 CTAs/SM, look-ahead 16, FP32 tile with cp.async staging), 400 pairs,
+# 5.01 GB of algorithmic input bytes.
 TRAFFIC_CAPTURE = {
-    1: {"bytes": 85.735969e9, "alg_bytes": 16898189704.0, "precision": "mixed_fp32"},
-    3: {"bytes": 17845812736.0 + 4430136576.0, "alg_bytes": 5011263536.0,
+    3: {"bytes": 17.657836e9 + 4.410247e9, "alg_bytes": 5011263536.0,
         "precision": "mixed_fp32"},
 }
 

@@ -12,8 +12,17 @@
 
 namespace pf12 {
 
+// Shared tiles of the CTA GEMM.  FP64 products: A and B as double[kBK][kTile
+// + 1].  FP32 products: A and B as float[kBK][kTileF] (rows 16-byte aligned
+// for vector loads), followed by the raw FP64 stage of the next K chunk
+// (16 values per thread, copied with cp.async while the current chunk is
+// computed).
+constexpr int kTileF = kTile + 4;
+constexpr int kTilesF64 = 2 * kBK * (kTile + 1);          // doubles
+constexpr int kRawOff = kBK * kTileF;                     // doubles (= 2 kBK kTileF floats)
+constexpr int kRawLen = 16 * kThreads;                    // doubles
 struct __align__(128) GemmSmem {
-  double buf[2 * kBK * (kTile + 1)];  // A and B tiles (as double or as float)
+  double buf[kTilesF64 > kRawOff + kRawLen ? kTilesF64 : kRawOff + kRawLen];
 };
 
 struct __align__(16) CholSmem {
@@ -29,39 +38,199 @@ struct __align__(16) CholSmem {
 //   B(t, c) = TB ? B[c * ldb + t] : B[t * ldb + c].
 // FP64 <-> FP32 conversions in integer arithmetic.  On this part the FP64 pipe
 // is the bottleneck and executes the hardware conversions too; these run on
-// the integer pipes instead.  Binary64 -> binary32 rounds to nearest, ties to
-// even: keep 23 of the 52 fraction bits, rebias the exponent (1023 -> 127) and
-// add one unit when the 29 dropped bits exceed half a unit, or equal it with
-// an odd kept fraction (a carry into the exponent is the correct result,
-// including the step to infinity).  Values whose result is not a normal
-// binary32 (zero, subnormal, infinity, NaN) take the hardware conversion.
+// the integer pipes instead, for every input (no hardware fallback, so that a
+// warp in an FP32 phase never queues behind the co-resident CTAs' DFMAs).
+// Binary64 -> binary32 rounds to nearest, ties to even: keep 23 of the 52
+// fraction bits, rebias the exponent (1023 -> 127) and add one unit when the
+// 29 dropped bits exceed half a unit, or equal it with an odd kept fraction (a
+// carry into the exponent is the correct result, including the step to
+// infinity).  Results below the binary32 normal range are rounded the same way
+// at the subnormal spacing 2^-149; exponents above it overflow to infinity;
+// NaN stays NaN.
 __device__ __forceinline__ float f64_to_f32_rne(double x) {
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
   const unsigned int hi = static_cast<unsigned int>(b >> 32), lo = static_cast<unsigned int>(b);
+  const unsigned int sign = hi & 0x80000000u;
   const unsigned int e = (hi >> 20) & 0x7ffu;
-  if (e < 1023u - 126u || e > 1023u + 127u) return __double2float_rn(x);
-  unsigned int r = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-  const unsigned int rest = lo & 0x1fffffffu;
-  r += (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ? 1u : 0u;
-  return __uint_as_float(r);
+  if (e - (1023u - 126u) <= 253u) {
+    // (hi, lo) << 3 keeps the low 9 exponent bits, e - 512 for these e, on
+    // top of the 23 kept fraction bits; rebias by 384 to e - 896
+    unsigned int r = (__funnelshift_l(lo, hi, 3) - (384u << 23)) | sign;
+    const unsigned int rest = lo & 0x1fffffffu;
+    // +1 when rest > half, or rest == half with an odd kept fraction
+    r += (rest + (r & 1u) + 0x0fffffffu) >> 29;
+    return __uint_as_float(r);
+  }
+  if (e == 0x7ffu)   // infinity, or NaN (quiet, sign kept)
+    return __uint_as_float(sign | ((b & 0xfffffffffffffull) ? 0x7fc00000u : 0x7f800000u));
+  if (e > 1023u + 127u) return __uint_as_float(sign | 0x7f800000u);
+  // binary32 subnormal or zero: significand * 2^(e - 1075) in units of 2^-149
+  const unsigned int shift = 926u - e;          // > 29 here; e = 0 is below any result
+  if (e == 0u || shift > 54u) return __uint_as_float(sign);
+  const unsigned long long m53 = (b & 0xfffffffffffffull) | (1ull << 52);
+  unsigned int q = static_cast<unsigned int>(m53 >> shift);
+  const unsigned long long rem = m53 & ((1ull << shift) - 1ull), half = 1ull << (shift - 1u);
+  q += (rem > half || (rem == half && (q & 1u))) ? 1u : 0u;
+  return __uint_as_float(sign | q);
 }
 
 // Binary32 -> binary64, exact: rebias the exponent (127 -> 1023) and widen the
-// fraction; zero, subnormal, infinity and NaN take the hardware conversion.
+// fraction; subnormals are normalised, infinity and NaN keep their class.
 __device__ __forceinline__ double f32_to_f64(float f) {
   const unsigned int u = __float_as_uint(f);
   const unsigned int e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return static_cast<double>(f);
-  const unsigned long long b = (static_cast<unsigned long long>(u & 0x80000000u) << 32) |
-                               (static_cast<unsigned long long>(e + 896u) << 52) |
-                               (static_cast<unsigned long long>(u & 0x7fffffu) << 29);
+  const unsigned long long sign = static_cast<unsigned long long>(u & 0x80000000u) << 32;
+  const unsigned long long frac = u & 0x7fffffu;
+  unsigned long long b;
+  if (e != 0u && e != 0xffu) {
+    b = sign | (static_cast<unsigned long long>(e + 896u) << 52) | (frac << 29);
+  } else if (e == 0xffu) {
+    b = sign | (0x7ffull << 52) | (frac << 29);
+  } else if (frac == 0u) {
+    b = sign;
+  } else {           // subnormal: frac * 2^-149 with its top bit at position n
+    const unsigned int n = 31u - static_cast<unsigned int>(__clz(static_cast<int>(frac)));
+    b = sign | (static_cast<unsigned long long>(n + 874u) << 52) |
+        ((frac << (52u - n)) & 0xfffffffffffffull);
+  }
   return __longlong_as_double(static_cast<long long>(b));
 }
 
-template <typename TC>
-__device__ __forceinline__ TC to_operand(double x) {
-  if constexpr (sizeof(TC) == sizeof(float)) return f64_to_f32_rne(x);
-  else return x;
+// FP32-product tile (TC = float): 256 threads as a 16 x 16 grid of 4 x 4
+// output blocks, rows 4 (tid / 16) + i, columns 4 (tid % 16) + j, fed by one
+// 16-byte shared load of A and one of B per K step (16 FFMAs).  FP64 operands
+// are copied to the raw stage with cp.async one chunk ahead (zero-filled
+// outside the matrices) and rounded to FP32 by the thread that copied them.
+// Partial sums over 128-wide K spans are accumulated as an FP32 pair hi + lo
+// with TwoSum and widened to FP64 once, in the epilogue, so no FP64
+// instruction runs before it.  No triangular restriction (tri_rows).
+template <bool TA, bool TB>
+__device__ __forceinline__ void cta_gemm_tile_f32(int M, int N, int K, const double* A,
+                                                  int64_t lda, const double* B, int64_t ldb,
+                                                  double* C, int64_t ldc, int r0, int c0,
+                                                  double alpha, bool accumulate, GemmSmem& sm) {
+  float (*as)[kTileF] = reinterpret_cast<float (*)[kTileF]>(sm.buf);
+  float (*bs)[kTileF] = reinterpret_cast<float (*)[kTileF]>(reinterpret_cast<float*>(sm.buf) + kBK * kTileF);
+  double* raw = sm.buf + kRawOff;
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+  const bool act = r0 + 4 * ty < M && c0 + 4 * tx < N;
+  // operand (t, r) of A and (t, c) of B staged by this thread as its s-th value
+  auto a_at = [&](int s, int& r, int& t) {
+    if (!TA) { t = tid & 31; r = (tid >> 5) + 8 * s; }
+    else     { r = tid & 63; t = (tid >> 6) + 4 * s; }
+  };
+  auto b_at = [&](int s, int& c, int& t) {
+    if (TB) { t = tid & 31; c = (tid >> 5) + 8 * s; }
+    else    { c = tid & 63; t = (tid >> 6) + 4 * s; }
+  };
+  auto issue_raw = [&](int k0) {
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      int r, t;
+      a_at(s, r, t);
+      const int gr = r0 + r, gt = k0 + t;
+      const bool ok = gr < M && gt < K;
+      const double* src = ok ? (TA ? A + (int64_t)gt * lda + gr : A + (int64_t)gr * lda + gt) : A;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(
+                       static_cast<uint32_t>(__cvta_generic_to_shared(raw + s * kThreads + tid))),
+                   "l"(src), "r"(ok ? 8 : 0)
+                   : "memory");
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      int c, t;
+      b_at(s, c, t);
+      const int gc = c0 + c, gt = k0 + t;
+      const bool ok = gc < N && gt < K;
+      const double* src = ok ? (TB ? B + (int64_t)gc * ldb + gt : B + (int64_t)gt * ldb + gc) : B;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(
+                       static_cast<uint32_t>(__cvta_generic_to_shared(raw + (8 + s) * kThreads + tid))),
+                   "l"(src), "r"(ok ? 8 : 0)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  float accf[4][4], acch[4][4], accl[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { accf[i][j] = 0.0f; acch[i][j] = 0.0f; accl[i][j] = 0.0f; }
+
+  issue_raw(0);
+  int chunk = 0;
+  for (int k0 = 0; k0 < K; k0 += kBK, ++chunk) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      int r, t;
+      a_at(s, r, t);
+      as[t][r] = f64_to_f32_rne(raw[s * kThreads + tid]);
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      int c, t;
+      b_at(s, c, t);
+      bs[t][c] = f64_to_f32_rne(raw[(8 + s) * kThreads + tid]);
+    }
+    if (k0 + kBK < K) issue_raw(k0 + kBK);   // in flight during this chunk's products
+    __syncthreads();
+    if (act) {
+      const int kn = min(kBK, K - k0);
+#pragma unroll 4
+      for (int kk = 0; kk < kn; ++kk) {
+        const float4 a = *reinterpret_cast<const float4*>(&as[kk][4 * ty]);
+        const float4 b = *reinterpret_cast<const float4*>(&bs[kk][4 * tx]);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) accf[i][j] = fmaf(av[i], bv[j], accf[i][j]);
+      }
+      if ((chunk & 3) == 3 || k0 + kBK >= K) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            // TwoSum (Knuth): sum + err == acch + accf exactly
+            const float x = acch[i][j], y = accf[i][j];
+            const float sum = __fadd_rn(x, y);
+            const float yy = __fsub_rn(sum, x);
+            const float err = __fadd_rn(__fsub_rn(x, __fsub_rn(sum, yy)), __fsub_rn(y, yy));
+            acch[i][j] = sum;
+            accl[i][j] = __fadd_rn(accl[i][j], err);
+            accf[i][j] = 0.0f;
+          }
+      }
+    }
+    __syncthreads();
+  }
+  if (!act) return;
+  // Epilogue.  A single K span leaves accl == 0 and acch exact, so a plain
+  // store of +-(acch) needs no FP64 instruction (the sign is a bit flip; alpha
+  // is compared by its bits).
+  const long long abits = __double_as_longlong(alpha);
+  const bool plain = !accumulate && K <= 4 * kBK &&
+                     (abits == 0x3ff0000000000000ll || abits == (long long)0xbff0000000000000ull);
+  const unsigned long long flip = (abits < 0) ? 0x8000000000000000ull : 0ull;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + 4 * ty + i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + 4 * tx + j;
+      if (c >= N) continue;
+      double* pc = C + (int64_t)r * ldc + c;
+      if (plain) {
+        *pc = __longlong_as_double(
+            (long long)((unsigned long long)__double_as_longlong(f32_to_f64(acch[i][j])) ^ flip));
+      } else {
+        const double v = f32_to_f64(acch[i][j]) + f32_to_f64(accl[i][j]);
+        *pc = accumulate ? fma(alpha, v, *pc) : alpha * v;
+      }
+    }
+  }
 }
 
 // The 64 x 64 tile is split into 32 blocks of 8 x 16.  A block is active when
@@ -71,18 +240,22 @@ __device__ __forceinline__ TC to_operand(double x) {
 // lr + 4i, columns lc + 8j, conflict-free shared-memory reads), so ragged
 // edges and the upper halves of diagonal tiles cost no arithmetic and the
 // remaining work is spread evenly over the warps.
-// TC is the product type: double (FP64 FMAs) or float (FP32 FMAs; partial sums
-// over 128-wide K spans are added to FP64 accumulators).  Operands may alias
-// C's array as long as the tile's own C entries are not read as A/B.  All
-// threads must call; the C stores follow the last barrier and are read back
-// only by the thread that wrote them.
+// TC is the product type: double (FP64 FMAs, this routine) or float (FP32
+// FMAs, cta_gemm_tile_f32, which has no triangular restriction).  Operands may
+// alias C's array as long as the tile's own C entries are not read as A/B.
+// All threads must call; the C stores follow the last barrier and are read
+// back only by the thread that wrote them.
 template <typename TC, bool TA, bool TB>
 __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double* A, int64_t lda,
                                               const double* B, int64_t ldb, double* C,
                                               int64_t ldc, int r0, int c0, double alpha,
                                               bool accumulate, GemmSmem& sm, int tri_rows = 0) {
-  TC (*as)[kTile + 1] = reinterpret_cast<TC (*)[kTile + 1]>(sm.buf);
-  TC (*bs)[kTile + 1] = reinterpret_cast<TC (*)[kTile + 1]>(sm.buf + kBK * (kTile + 1));
+  if constexpr (sizeof(TC) != sizeof(double)) {
+    cta_gemm_tile_f32<TA, TB>(M, N, K, A, lda, B, ldb, C, ldc, r0, c0, alpha, accumulate, sm);
+    return;
+  } else {
+  double (*as)[kTile + 1] = reinterpret_cast<double (*)[kTile + 1]>(sm.buf);
+  double (*bs)[kTile + 1] = reinterpret_cast<double (*)[kTile + 1]>(sm.buf + kBK * (kTile + 1));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int lr = lane >> 3, lc = lane & 7;
   // this warp's blocks: tile-local origins (row, col); -1 = unused slot
@@ -106,24 +279,22 @@ __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double*
   }
   const bool any = orow[0] >= 0;
   double accd[4][2][2];
-  float accf[4][2][2];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int j = 0; j < 2; ++j) { accd[q][i][j] = 0.0; accf[q][i][j] = 0.0f; }
+      for (int j = 0; j < 2; ++j) accd[q][i][j] = 0.0;
 
-  int chunk = 0;
-  for (int k0 = 0; k0 < K; k0 += kBK, ++chunk) {
+  for (int k0 = 0; k0 < K; k0 += kBK) {
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       int r, t;
       if (!TA) { t = tid & 31; r = (tid >> 5) + 8 * s; }
       else     { r = tid & 63; t = (tid >> 6) + 4 * s; }
       const int gr = r0 + r, gt = k0 + t;
-      TC v = TC(0);
-      if (gr < M && gt < K) v = to_operand<TC>(TA ? A[(int64_t)gt * lda + gr] : A[(int64_t)gr * lda + gt]);
+      double v = 0.0;
+      if (gr < M && gt < K) v = TA ? A[(int64_t)gt * lda + gr] : A[(int64_t)gr * lda + gt];
       as[t][r] = v;
     }
 #pragma unroll
@@ -132,51 +303,24 @@ __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double*
       if (TB) { t = tid & 31; c = (tid >> 5) + 8 * s; }
       else    { c = tid & 63; t = (tid >> 6) + 4 * s; }
       const int gc = c0 + c, gt = k0 + t;
-      TC v = TC(0);
-      if (gc < N && gt < K) v = to_operand<TC>(TB ? B[(int64_t)gc * ldb + gt] : B[(int64_t)gt * ldb + gc]);
+      double v = 0.0;
+      if (gc < N && gt < K) v = TB ? B[(int64_t)gc * ldb + gt] : B[(int64_t)gt * ldb + gc];
       bs[t][c] = v;
     }
     __syncthreads();
     if (any) {
       const int kn = min(kBK, K - k0);
-      if constexpr (sizeof(TC) == sizeof(double)) {
 #pragma unroll 4
-        for (int kk = 0; kk < kn; ++kk) {
+      for (int kk = 0; kk < kn; ++kk) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (orow[q] < 0) continue;
-            const double a0 = as[kk][orow[q] + lr], a1 = as[kk][orow[q] + lr + 4];
-            const double b0 = bs[kk][ocol[q] + lc], b1 = bs[kk][ocol[q] + lc + 8];
-            accd[q][0][0] = fma(a0, b0, accd[q][0][0]);
-            accd[q][0][1] = fma(a0, b1, accd[q][0][1]);
-            accd[q][1][0] = fma(a1, b0, accd[q][1][0]);
-            accd[q][1][1] = fma(a1, b1, accd[q][1][1]);
-          }
-        }
-      } else {
-#pragma unroll 4
-        for (int kk = 0; kk < kn; ++kk) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (orow[q] < 0) continue;
-            const float a0 = as[kk][orow[q] + lr], a1 = as[kk][orow[q] + lr + 4];
-            const float b0 = bs[kk][ocol[q] + lc], b1 = bs[kk][ocol[q] + lc + 8];
-            accf[q][0][0] = fmaf(a0, b0, accf[q][0][0]);
-            accf[q][0][1] = fmaf(a0, b1, accf[q][0][1]);
-            accf[q][1][0] = fmaf(a1, b0, accf[q][1][0]);
-            accf[q][1][1] = fmaf(a1, b1, accf[q][1][1]);
-          }
-        }
-        if ((chunk & 3) == 3 || k0 + kBK >= K) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-              for (int j = 0; j < 2; ++j) {
-                if (orow[q] >= 0) accd[q][i][j] += f32_to_f64(accf[q][i][j]);
-                accf[q][i][j] = 0.0f;
-              }
+        for (int q = 0; q < 4; ++q) {
+          if (orow[q] < 0) continue;
+          const double a0 = as[kk][orow[q] + lr], a1 = as[kk][orow[q] + lr + 4];
+          const double b0 = bs[kk][ocol[q] + lc], b1 = bs[kk][ocol[q] + lc + 8];
+          accd[q][0][0] = fma(a0, b0, accd[q][0][0]);
+          accd[q][0][1] = fma(a0, b1, accd[q][0][1]);
+          accd[q][1][0] = fma(a1, b0, accd[q][1][0]);
+          accd[q][1][1] = fma(a1, b1, accd[q][1][1]);
         }
       }
     }
@@ -197,6 +341,7 @@ __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double*
         *pc = accumulate ? fma(alpha, accd[q][i][j], *pc) : alpha * accd[q][i][j];
       }
     }
+  }
   }
 }
 
