@@ -101,9 +101,11 @@ __device__ __forceinline__ double f32_to_f64(float f) {
 // 16-byte shared load of A and one of B per K step (16 FFMAs).  FP64 operands
 // are copied to the raw stage with cp.async one chunk ahead (zero-filled
 // outside the matrices) and rounded to FP32 by the thread that copied them.
-// Partial sums over 128-wide K spans are accumulated as an FP32 pair hi + lo
-// with TwoSum and widened to FP64 once, in the epilogue, so no FP64
-// instruction runs before it.  No triangular restriction (tri_rows).
+// Two-level FP32 summation: each 32-wide K chunk is summed on its own and
+// then added to a running sum, so the rounding error grows as
+// sqrt(32 + K / 32) units instead of sqrt(K); the sum is widened to FP64 once,
+// in the epilogue, and no FP64 instruction runs before it (none at all for a
+// plain store with alpha = +-1).  No triangular restriction (tri_rows).
 template <bool TA, bool TB>
 __device__ __forceinline__ void cta_gemm_tile_f32(int M, int N, int K, const double* A,
                                                   int64_t lda, const double* B, int64_t ldb,
@@ -151,15 +153,14 @@ __device__ __forceinline__ void cta_gemm_tile_f32(int M, int N, int K, const dou
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
-  float accf[4][4], acch[4][4], accl[4][4];
+  float accf[4][4], accs[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { accf[i][j] = 0.0f; acch[i][j] = 0.0f; accl[i][j] = 0.0f; }
+    for (int j = 0; j < 4; ++j) { accf[i][j] = 0.0f; accs[i][j] = 0.0f; }
 
   issue_raw(0);
-  int chunk = 0;
-  for (int k0 = 0; k0 < K; k0 += kBK, ++chunk) {
+  for (int k0 = 0; k0 < K; k0 += kBK) {
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
@@ -187,31 +188,22 @@ __device__ __forceinline__ void cta_gemm_tile_f32(int M, int N, int K, const dou
 #pragma unroll
           for (int j = 0; j < 4; ++j) accf[i][j] = fmaf(av[i], bv[j], accf[i][j]);
       }
-      if ((chunk & 3) == 3 || k0 + kBK >= K) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            // TwoSum (Knuth): sum + err == acch + accf exactly
-            const float x = acch[i][j], y = accf[i][j];
-            const float sum = __fadd_rn(x, y);
-            const float yy = __fsub_rn(sum, x);
-            const float err = __fadd_rn(__fsub_rn(x, __fsub_rn(sum, yy)), __fsub_rn(y, yy));
-            acch[i][j] = sum;
-            accl[i][j] = __fadd_rn(accl[i][j], err);
-            accf[i][j] = 0.0f;
-          }
-      }
+        for (int j = 0; j < 4; ++j) {
+          accs[i][j] = __fadd_rn(accs[i][j], accf[i][j]);
+          accf[i][j] = 0.0f;
+        }
     }
     __syncthreads();
   }
   if (!act) return;
-  // Epilogue.  A single K span leaves accl == 0 and acch exact, so a plain
-  // store of +-(acch) needs no FP64 instruction (the sign is a bit flip; alpha
-  // is compared by its bits).
+  // Epilogue: a plain store of +-(sum) needs no FP64 instruction (the sign is
+  // a bit flip; alpha is compared by its bits).
   const long long abits = __double_as_longlong(alpha);
-  const bool plain = !accumulate && K <= 4 * kBK &&
-                     (abits == 0x3ff0000000000000ll || abits == (long long)0xbff0000000000000ull);
+  const bool plain = !accumulate && (abits == 0x3ff0000000000000ll ||
+                                     abits == (long long)0xbff0000000000000ull);
   const unsigned long long flip = (abits < 0) ? 0x8000000000000000ull : 0ull;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -222,13 +214,12 @@ __device__ __forceinline__ void cta_gemm_tile_f32(int M, int N, int K, const dou
       const int c = c0 + 4 * tx + j;
       if (c >= N) continue;
       double* pc = C + (int64_t)r * ldc + c;
-      if (plain) {
+      const double v = f32_to_f64(accs[i][j]);
+      if (plain)
         *pc = __longlong_as_double(
-            (long long)((unsigned long long)__double_as_longlong(f32_to_f64(acch[i][j])) ^ flip));
-      } else {
-        const double v = f32_to_f64(acch[i][j]) + f32_to_f64(accl[i][j]);
+            (long long)((unsigned long long)__double_as_longlong(v) ^ flip));
+      else
         *pc = accumulate ? fma(alpha, v, *pc) : alpha * v;
-      }
     }
   }
 }

@@ -9,6 +9,7 @@ pf12_upload_pairs / pf12_fit / pf12_energy path within the FP64 parity bar.
 This file is collected last so that a failure here leaves every other test run.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -128,14 +129,21 @@ def test_noalloc_refuses_a_capturing_stream(built):
     s = torch.cuda.Stream()
     g = torch.cuda.CUDAGraph()
     x = torch.zeros(4, device="cuda")
+    # an engine left unreferenced by an earlier test must not be finalised
+    # (device frees) inside the capture: collect now, no collection during it
+    gc.collect()
     torch.cuda.synchronize()
-    with torch.cuda.stream(s):
-        g.capture_begin()
-        try:
-            x.add_(1.0)
-            rc, _ = _call(lib, wl, t, lay, "fp64", V, e)
-        finally:
-            g.capture_end()
+    gc.disable()
+    try:
+        with torch.cuda.stream(s):
+            g.capture_begin()
+            try:
+                x.add_(1.0)
+                rc, _ = _call(lib, wl, t, lay, "fp64", V, e)
+            finally:
+                g.capture_end()
+    finally:
+        gc.enable()
     assert rc == -7
     g.replay()                       # the caller's capture is intact
     torch.cuda.synchronize()
