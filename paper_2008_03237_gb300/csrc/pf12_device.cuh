@@ -833,19 +833,55 @@ __device__ __forceinline__ long long next_slot(const FwdParams& prm, int& known_
 // (row r holds J[r][0..r] at r (r + 1) / 2): a symmetric metric then travels
 // and rests in about half the bytes.
 
-// J_g into the top m rows of M (row stride ld).  Packed: the lower triangle
-// only, which is all the Cholesky reads.
+// Copy of a rows x cols block (lower = false) or of the lower triangle of a
+// square block, diagonal included (lower = true), from global memory into the
+// slab (row stride dld).  The source rows have stride sld, or, with packed
+// (lower only), are the packed lower triangle (row r at r (r + 1) / 2).  All
+// threads walk the region in row-major order, 256 elements apart, with eight
+// loads in flight each before their stores: the copy is bound by memory
+// latency, not bandwidth.
+__device__ __forceinline__ void copy_region(const double* src, int64_t sld, int rows, int cols,
+                                            bool lower, bool packed, double* dst, int64_t dld) {
+  constexpr int kU = 8;
+  if (rows <= 0 || cols <= 0) return;
+  auto advance = [&](int& r, int& c, int step) {
+    c += step;
+    while (r < rows) {
+      const int len = lower ? r + 1 : cols;
+      if (c < len) break;
+      c -= len;
+      ++r;
+    }
+  };
+  int r = 0, c = static_cast<int>(threadIdx.x);
+  advance(r, c, 0);
+  while (r < rows) {
+    double v[kU];
+    int rr = r, cc = c;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t at = packed ? (int64_t)rr * (rr + 1) / 2 + cc : (int64_t)rr * sld + cc;
+      v[u] = (rr < rows) ? src[at] : 0.0;
+      advance(rr, cc, kThreads);
+    }
+    rr = r;
+    cc = c;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (rr < rows) dst[(int64_t)rr * dld + cc] = v[u];
+      advance(rr, cc, kThreads);
+    }
+    r = rr;
+    c = cc;
+  }
+}
+
+// J_g (full or packed lower triangle) into the slab's leading m x m block:
+// only the lower triangle, diagonal included, which is all the factorisation
+// and the solves read; the entries above the diagonal are scratch.
 __device__ __forceinline__ void load_metric(const double* J, int m, bool packed, double* M,
                                             int64_t ld) {
-  const int lane = threadIdx.x & 31;
-  for (int r = threadIdx.x >> 5; r < m; r += kThreads / 32) {
-    if (packed) {
-      const double* row = J + (int64_t)r * (r + 1) / 2;
-      for (int c = lane; c <= r; c += 32) M[(int64_t)r * ld + c] = row[c];
-    } else {
-      for (int c = lane; c < m; c += 32) M[(int64_t)r * ld + c] = J[(int64_t)r * m + c];
-    }
-  }
+  copy_region(J, m, m, m, /*lower=*/true, packed, M, ld);
 }
 
 // Full symmetric m x m J_f (row stride ld) from its packed lower triangle.

@@ -33,9 +33,7 @@ namespace pf12 {
 // rows x cols block from global memory (row stride sld) into the slab (row stride dld)
 __device__ __forceinline__ void copy_block(const double* src, int64_t sld, int rows, int cols,
                                            double* dst, int64_t dld) {
-  const int lane = threadIdx.x & 31;
-  for (int r = threadIdx.x >> 5; r < rows; r += kThreads / 32)
-    for (int c = lane; c < cols; c += 32) dst[(int64_t)r * dld + c] = src[(int64_t)r * sld + c];
+  copy_region(src, sld, rows, cols, /*lower=*/false, /*packed=*/false, dst, dld);
 }
 
 // Q_x^T A for a (p + 2)-row block: the PNO rows through Q, rows p, p + 1 copied
@@ -77,7 +75,7 @@ __device__ void pair_full(const FullParams& prm, const FullDesc& pd, double* ws,
   const double* ArjF = prm.ArjF + pd.off_pm;
 
   // 1. J_g and the Coulomb factors into the slab; FP64 factorisation + solves
-  copy_block(Jg, m, m, m, M, ld);
+  load_metric(Jg, m, false, M, ld);   // lower triangle: all the factorisation reads
   copy_block(Agi, m, p + 2, m, M + r_i * ld, ld);
   copy_block(Agj, m, p + 2, m, M + r_j * ld, ld);
   copy_block(AgiF, m, p, m, M + r_iF * ld, ld);
