@@ -224,23 +224,30 @@ __device__ __forceinline__ void cta_gemm_tile_f32(int M, int N, int K, const dou
   }
 }
 
-// The 64 x 64 tile is split into 32 blocks of 8 x 16.  A block is active when
-// it meets [0, M) x [0, N) and, if tri_rows > 0, is not entirely above the
-// diagonal within the first tri_rows rows.  Active blocks are dealt
-// round-robin to the 8 warps (at most 4 each; lane: 2 x 2 outputs, rows
-// lr + 4i, columns lc + 8j, conflict-free shared-memory reads), so ragged
-// edges and the upper halves of diagonal tiles cost no arithmetic and the
-// remaining work is spread evenly over the warps.
+// The 64 x 64 tile is split into 32 blocks of RB x (128 / RB): 8 x 16 by
+// default, 4 x 32 for products with few rows (the triangular solves' 2k
+// right-hand sides, where 8-row blocks would carry up to 6 rows of zeros).  A
+// block is active when it meets [0, M) x [0, N) and, if tri_rows > 0, is not
+// entirely above the diagonal within the first tri_rows rows.  Active blocks
+// are dealt round-robin to the 8 warps (at most 4 each; lane: 2 x 2 outputs,
+// rows lr + (RB / 2) i, columns lc + (64 / RB) j, conflict-free shared-memory
+// reads), so ragged edges and the upper halves of diagonal tiles cost no
+// arithmetic and the remaining work is spread evenly over the warps.
 // TC is the product type: double (FP64 FMAs, this routine) or float (FP32
 // FMAs, cta_gemm_tile_f32, which has no triangular restriction).  Operands may
 // alias C's array as long as the tile's own C entries are not read as A/B.
 // All threads must call; the C stores follow the last barrier and are read
 // back only by the thread that wrote them.
-template <typename TC, bool TA, bool TB>
+template <typename TC, bool TA, bool TB, int RB = 8>
 __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double* A, int64_t lda,
                                               const double* B, int64_t ldb, double* C,
                                               int64_t ldc, int r0, int c0, double alpha,
                                               bool accumulate, GemmSmem& sm, int tri_rows = 0) {
+  static_assert(RB == 8 || RB == 4, "row block of 8 or 4");
+  constexpr int CB = 128 / RB;       // block columns
+  constexpr int LC = CB / 2;         // lanes along a block's columns
+  constexpr int LR = 32 / LC;        // lanes along its rows (= RB / 2)
+  constexpr int NCB = kTile / CB;    // blocks across the tile
   if constexpr (sizeof(TC) != sizeof(double)) {
     cta_gemm_tile_f32<TA, TB>(M, N, K, A, lda, B, ldb, C, ldc, r0, c0, alpha, accumulate, sm);
     return;
@@ -248,20 +255,20 @@ __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double*
   double (*as)[kTile + 1] = reinterpret_cast<double (*)[kTile + 1]>(sm.buf);
   double (*bs)[kTile + 1] = reinterpret_cast<double (*)[kTile + 1]>(sm.buf + kBK * (kTile + 1));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int lr = lane >> 3, lc = lane & 7;
+  const int lr = lane / LC, lc = lane % LC;
   // this warp's blocks: tile-local origins (row, col); -1 = unused slot
   int orow[4] = {-1, -1, -1, -1}, ocol[4] = {0, 0, 0, 0};
   {
     int cnt = 0, slot = 0;
 #pragma unroll
     for (int b = 0; b < 32; ++b) {
-      const int br = r0 + 8 * (b >> 2), bc = c0 + 16 * (b & 3);
+      const int br = r0 + RB * (b / NCB), bc = c0 + CB * (b % NCB);
       bool act = br < M && bc < N;
-      if (tri_rows > 0 && br + 7 < tri_rows && bc > br + 7) act = false;
+      if (tri_rows > 0 && br + RB - 1 < tri_rows && bc > br + RB - 1) act = false;
       if (act) {
         if ((cnt & 7) == warp && slot < 4) {
-          orow[slot] = 8 * (b >> 2);
-          ocol[slot] = 16 * (b & 3);
+          orow[slot] = RB * (b / NCB);
+          ocol[slot] = CB * (b % NCB);
           ++slot;
         }
         ++cnt;
@@ -306,8 +313,8 @@ __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double*
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           if (orow[q] < 0) continue;
-          const double a0 = as[kk][orow[q] + lr], a1 = as[kk][orow[q] + lr + 4];
-          const double b0 = bs[kk][ocol[q] + lc], b1 = bs[kk][ocol[q] + lc + 8];
+          const double a0 = as[kk][orow[q] + lr], a1 = as[kk][orow[q] + lr + LR];
+          const double b0 = bs[kk][ocol[q] + lc], b1 = bs[kk][ocol[q] + lc + LC];
           accd[q][0][0] = fma(a0, b0, accd[q][0][0]);
           accd[q][0][1] = fma(a0, b1, accd[q][0][1]);
           accd[q][1][0] = fma(a1, b0, accd[q][1][0]);
@@ -322,11 +329,11 @@ __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double*
     if (orow[q] < 0) continue;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-      const int r = r0 + orow[q] + lr + 4 * i;
+      const int r = r0 + orow[q] + lr + LR * i;
       if (r >= M) continue;
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const int c = c0 + ocol[q] + lc + 8 * j;
+        const int c = c0 + ocol[q] + lc + LC * j;
         if (c >= N) continue;
         double* pc = C + (int64_t)r * ldc + c;
         *pc = accumulate ? fma(alpha, accd[q][i][j], *pc) : alpha * accd[q][i][j];
@@ -337,13 +344,14 @@ __device__ __forceinline__ void cta_gemm_tile(int M, int N, int K, const double*
 }
 
 // Whole-matrix product over all 64 x 64 output tiles of an M x N result.
-template <typename TC, bool TA, bool TB>
+template <typename TC, bool TA, bool TB, int RB = 8>
 __device__ __forceinline__ void cta_gemm(int M, int N, int K, const double* A, int64_t lda,
                                          const double* B, int64_t ldb, double* C, int64_t ldc,
                                          double alpha, bool accumulate, GemmSmem& sm) {
   for (int r0 = 0; r0 < M; r0 += kTile)
     for (int c0 = 0; c0 < N; c0 += kTile)
-      cta_gemm_tile<TC, TA, TB>(M, N, K, A, lda, B, ldb, C, ldc, r0, c0, alpha, accumulate, sm);
+      cta_gemm_tile<TC, TA, TB, RB>(M, N, K, A, lda, B, ldb, C, ldc, r0, c0, alpha, accumulate,
+                                    sm);
   __syncthreads();
 }
 
@@ -513,14 +521,14 @@ __device__ __forceinline__ void solve_right_lower(const double* L, int64_t ld, i
     for (int cb = gb_hi - 1; cb >= gb_lo; --cb) {
       const int c0 = cb * kNB, nb = min(kNB, m - c0), cend = c0 + nb;
       if (cend < g1) {   // Y_blk -= X[:, cend:g1] L[cend:g1, blk]
-        cta_gemm<double, false, false>(nrows, nb, g1 - cend, Y + cend, ldy,
+        cta_gemm<double, false, false, 4>(nrows, nb, g1 - cend, Y + cend, ldy,
                                        L + (int64_t)cend * ld + c0, ld, Y + c0, ldy, -1.0, true, gs);
         __syncthreads();
       }
       solve_block<false>(L, ld, Y, ldy, nrows, c0, nb, cs);
     }
     if (g0 > 0) {        // Y[:, 0:g0] -= X[:, g0:g1] L[g0:g1, 0:g0]
-      cta_gemm<double, false, false>(nrows, g0, g1 - g0, Y + g0, ldy, L + (int64_t)g0 * ld, ld, Y,
+      cta_gemm<double, false, false, 4>(nrows, g0, g1 - g0, Y + g0, ldy, L + (int64_t)g0 * ld, ld, Y,
                                      ldy, -1.0, true, gs);
       __syncthreads();
     }
@@ -537,14 +545,14 @@ __device__ __forceinline__ void solve_right_lowerT(const double* L, int64_t ld, 
     for (int kb = g0; kb < g1; kb += kNB) {
       const int nb = min(kNB, m - kb);
       if (kb > g0) {     // Y_blk -= X[:, g0:kb] L[blk, g0:kb]^T
-        cta_gemm<double, false, true>(nrows, nb, kb - g0, Y + g0, ldy, L + (int64_t)kb * ld + g0,
+        cta_gemm<double, false, true, 4>(nrows, nb, kb - g0, Y + g0, ldy, L + (int64_t)kb * ld + g0,
                                       ld, Y + kb, ldy, -1.0, true, gs);
         __syncthreads();
       }
       solve_block<true>(L, ld, Y, ldy, nrows, kb, nb, cs);
     }
     if (g1 < m) {        // Y[:, g1:m] -= X[:, g0:g1] L[g1:m, g0:g1]^T
-      cta_gemm<double, false, true>(nrows, m - g1, g1 - g0, Y + g0, ldy, L + (int64_t)g1 * ld + g0,
+      cta_gemm<double, false, true, 4>(nrows, m - g1, g1 - g0, Y + g0, ldy, L + (int64_t)g1 * ld + g0,
                                     ld, Y + g1, ldy, -1.0, true, gs);
       __syncthreads();
     }
