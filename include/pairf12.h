@@ -67,10 +67,12 @@ extern "C" {
  * FP64 Cholesky, solves and energy sums in every mode. */
 typedef enum {
   PF12_FP64 = 0,       /* everything FP64 (plain mode) */
-  PF12_MIXED_FP32 = 2  /* FP32-class products with FP64 accumulation: FP32 FFMA
-                          (promoted every 128 of K), or, when the autotuner picks the
+  PF12_MIXED_FP32 = 2  /* FP32-class products: FP32 FFMA summed in two levels (each
+                          32-wide K chunk, then a running FP32 sum), widened to FP64
+                          once per output; or, when the autotuner picks the
                           tensor-core variant, tcgen05 split-TF32 (hi + lo, 3 products)
-                          for the projections and the J_f product (promoted every 32) */
+                          for the projections and the J_f product, added into FP64
+                          every 32 of K */
 } pf12_precision;
 
 typedef struct pf12_ctx pf12_ctx; /* opaque, library-owned */
