@@ -3,9 +3,11 @@
 Bars: FP64 mode within 1e-10 Eh per pair; mixed mode within 1 uEh in total
 after the chemical-scale normalisation (reading G1); FP64 gradients within
 1e-10 of the oracle's, relative to the largest entry of each block; mixed-mode
-gradients within 2e-5 (the error model of the FP32 products: about
-sqrt(128) 2^-24 per promoted 128-wide span, amplified by cond(J_g) ~ 40 in the
-solves, so 0.75 cond(J_g) sqrt(128) 2^-24).
+gradients within 2e-5, 0.75 cond(J_g) sqrt(128) 2^-24 with cond(J_g) ~ 40.
+The error model of the FP32 products: two-level FP32 sums (32-wide chunks
+added to a running sum) carry about sqrt(32 + K/32) 2^-24, at most
+8.9 2^-24 for K <= 1500, below the sqrt(128) 2^-24 the bar was derived from,
+and the solves amplify it by cond(J_g).
 """
 import os
 
