@@ -159,7 +159,7 @@ __device__ __forceinline__ void cta_gemm_tile_f32(int M, int N, int K, const dou
 #pragma unroll
     for (int j = 0; j < 4; ++j) { accf[i][j] = 0.0f; accs[i][j] = 0.0f; }
 
-  issue_raw(0);
+  if (K > 0) issue_raw(0);   // K = 0: no copy in flight; the epilogue stores +-0
   for (int k0 = 0; k0 < K; k0 += kBK) {
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 #pragma unroll
